@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Benchmark of bulk generation with libxr on GB300.
+
+One step = the whole path over one batch: for each of the 8 generators and
+each output type (native word, double) -- seed a base state with SplitMix64(42),
+jump-start 2^20 streams (stream i = J^(first + i)(base)), and fill 2^20 x 2^10
+outputs.  Every step writes 120 GiB of output.  `value` is generated bytes per
+second (GB/s, 1e9) over all ranks with the inputs already on the device;
+`e2e` repeats the step through the host-buffer entry point, device-to-host
+copies included.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xr|reference]
+
+Under torchrun every rank is an independent replica over a disjoint range of
+stream indices (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "generated GB/s & % of HBM roofline (batched vs plain, 1 GB300); p50/p99 latency"
+UNIT = "GB/s"
+FILL_SOURCES = ("paper_1805_01407_gb300/csrc/xr_fill_impl.cuh", "paper_1805_01407_gb300/csrc/xr_device.cuh")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["xr", "reference"], default="xr")
+    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--profile", choices=["fill", "streams"], default=None,
+                   help="run a small case for an ncu capture instead of the benchmark")
+    p.add_argument("--profile-variant", default="xoshiro256**")
+    p.add_argument("--profile-dtype", default=None)
+    p.add_argument("--profile-streams", type=int, default=1 << 16)
+    p.add_argument("--profile-launches", type=int, default=3)
+    return p.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def jobs():
+    return [(v, d) for v in W.CONFIG_BULK["variants"] for d in (W.native_dtype(v), "f64")]
+
+
+def dtype_bytes(d):
+    return 8 if d in ("u64", "f64") else 4
+
+
+def state_bytes(v):
+    return 32 if v.startswith("xoshiro256") else 16
+
+
+def workload_config(world):
+    c = W.CONFIG_BULK
+    S, m = c["S"], c["m"]
+    nbytes = sum(S * m * dtype_bytes(d) for _, d in jobs())
+    return {
+        "workload": "bulk fill: 8 generators (xoshiro256+/++/**, xoroshiro128+/++/**, "
+                    "xoshiro128**/++) x {native word, f64}; 2^20 streams x 2^10 outputs per job "
+                    "(2^30 values); SplitMix64(42) base; stream i = J^(first+i)(base)",
+        "streams": S, "outputs_per_stream": m, "jobs_per_step": len(jobs()),
+        "values_per_step": len(jobs()) * S * m, "bytes_per_step": nbytes,
+        "global_batch": world * len(jobs()) * S * m, "seq_len": m,
+        "l2": "each launch writes 4-8 GiB, far larger than the 129 MB L2; no flush needed",
+        "parallelism": "replicas over disjoint stream ranges" if world > 1 else "single GPU",
+    }, nbytes
+
+
+# ---------------------------------------------------------------- clocks
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="xr_clocks_", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + CLOCK_FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "nvidia-smi unavailable"}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = [n for k, n in enumerate(names) if any(r[5 + k].lower() == "active" for r in rows)]
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(rows[0][2]), "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------- roofline inputs
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def fill_source_hash():
+    h = hashlib.sha256()
+    for p in FILL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per fill launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "fill_traffic.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha") != fill_source_hash():
+            return None
+        return {"bytes_per_launch": float(kv["dram_bytes_per_launch_full_size"]),
+                "algorithmic_bytes_per_launch": float(kv.get("algorithmic_bytes_per_launch", "nan"))}
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- oracle timing
+
+def oracle_sample(streams, m, seed):
+    """Run the oracle on `streams` streams per job; returns (bytes, seconds)."""
+    import oracle as O
+    nbytes, t0 = 0, time.perf_counter()
+    for v, d in jobs():
+        base = O.seed(v, seed)
+        raw = O.bulk_fill(v, "jump", base, streams, m)
+        if d == "f64":
+            O.to_f64(v, raw)
+        nbytes += streams * m * dtype_bytes(d)
+    return nbytes, time.perf_counter() - t0
+
+
+def cpu_baseline(seconds):
+    m, seed = W.CONFIG_BULK["m"], W.CONFIG_BULK["seed"]
+    b, t = oracle_sample(64, m, seed)
+    streams = max(64, int(64 * seconds / max(t, 1e-3)))
+    b, t = oracle_sample(streams, m, seed)
+    return {"value": b / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "16 jobs (8 generators x {native, f64}) x %d streams x %d outputs "
+                      "(stream i = J^i(SplitMix64(42)) by one jump after another), single-threaded "
+                      "plain C oracle, %.1f s" % (streams, m, t),
+            "seconds": t, "bytes": b}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    cfg, _ = workload_config(1)
+    m, seed = W.CONFIG_BULK["m"], W.CONFIG_BULK["seed"]
+    streams = 1024
+    for _ in range(args.warmup):
+        oracle_sample(streams, m, seed)
+    tot_b, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        b, t = oracle_sample(streams, m, seed)
+        tot_b += b
+        tot_t += t
+    value = tot_b / tot_t / 1e9
+    sample = ("each step: 16 jobs (8 generators x {native, f64}) x %d streams x %d outputs, "
+              "single-threaded plain C oracle" % (streams, m))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": cfg, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- libxr arm
+
+def run_xr(args):
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1805_01407_gb300 as xr
+    from paper_1805_01407_gb300 import build as libbuild
+    libbuild.build()
+
+    cfg, bytes_per_step = workload_config(world)
+    c = W.CONFIG_BULK
+    S, m, seed = c["S"], c["m"], c["seed"]
+    first = rank * S
+    ctx = xr.Context(local)
+    stream = torch.cuda.current_stream()
+    base = ctx.empty_states("xoshiro256**", 1)
+    states = ctx.empty_states("xoshiro256**", S)
+    out = torch.empty(S * m * 8, dtype=torch.uint8, device="cuda")
+    views = {d: out.view(xr.torch_dtype(d)) for d in ("u64", "u32", "f64")}
+    J = jobs()
+
+    def new_events():
+        return [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in J]
+
+    def step(evs=None):
+        for j, (v, d) in enumerate(J):
+            ctx.seed(v, seed, base)
+            if evs:
+                evs[j][0].record(stream)
+            ctx.make_streams(v, "jump", base, first, S, states)
+            if evs:
+                evs[j][1].record(stream)
+            ctx.fill(v, states, S, m, d, views[d])
+            if evs:
+                evs[j][2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+
+    # store-only reference: cudaMemset of the same 8 GiB buffer
+    t_ms = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out.zero_()
+        b.record(stream)
+        b.synchronize()
+        t_ms.append(a.elapsed_time(b))
+    memset_gbs = out.numel() / (min(t_ms) / 1e3) / 1e9
+
+    step_events = [new_events() for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    n0 = xr.launch_count()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(step_events[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = xr.launch_count() - n0
+    elapsed_ms = t0.elapsed_time(t1)
+    clk = clocks.stop()
+    fill_ms = {jd: [step_events[k][j][1].elapsed_time(step_events[k][j][2]) for k in range(args.steps)]
+               for j, jd in enumerate(J)}
+    mk_ms = {jd: [step_events[k][j][0].elapsed_time(step_events[k][j][1]) for k in range(args.steps)]
+             for j, jd in enumerate(J)}
+    if dist:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    status = ctx.status()
+
+    value = world * bytes_per_step * args.steps / (elapsed_ms / 1e3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    fill_bytes = fill_time = 0.0
+    per_job = {}
+    for (v, d), times in fill_ms.items():
+        alg = S * m * dtype_bytes(d) + S * state_bytes(v)
+        fill_bytes += alg * len(times)
+        fill_time += sum(times) / 1e3
+        per_job["%s/%s" % (v, d)] = {"fill_ms": statistics.median(times),
+                                     "fill_gbs": alg / (statistics.median(times) / 1e3) / 1e9,
+                                     "streams_ms": statistics.median(mk_ms[(v, d)])}
+    achieved = fill_bytes / fill_time / 1e9
+    traffic = recorded_traffic()
+    mk_total = sum(sum(t) for t in mk_ms.values()) / args.steps
+    fill_total = sum(sum(t) for t in fill_ms.values()) / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": cfg, "impl": "xr",
+        "outputs_per_s": world * cfg["values_per_step"] * args.steps / (elapsed_ms / 1e3),
+        "roofline": {"bound": "hbm", "kernel": "k_fill_tma (all 16 jobs)", "achieved": achieved,
+                     "peak": peak, "peak_kind": "%s hbm_gbs (copy, read+write)" % peak_kind,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic["bytes_per_launch"] if traffic else None,
+                     "algorithmic_bytes_per_launch_u64": S * m * 8 + S * 32,
+                     "memset_gbs": memset_gbs, "frac_of_memset": achieved / memset_gbs},
+        "step_breakdown_ms": {"fill": fill_total, "make_streams": mk_total,
+                              "other": elapsed_ms / args.steps - fill_total - mk_total},
+        "per_job": per_job,
+        "clocks": clk, "gpu_launches": launches, "status": status,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(ctx, args, first, bytes_per_step, world, dist)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_e2e(ctx, args, first, bytes_per_step, world, dist):
+    """The same step through xr_fill_host: each job's base state goes from host
+    memory to the device, its outputs come back into one pinned host buffer;
+    both copies are inside the timed region (wall clock around blocking calls)."""
+    import torch
+    c = W.CONFIG_BULK
+    S, m, seed = c["S"], c["m"], c["seed"]
+    host_base = {}
+    for v, _ in jobs():
+        if v not in host_base:
+            t = ctx.empty_states(v, 1)
+            ctx.seed(v, seed, t)
+            host_base[v] = ctx.get_state(v, t)
+    h_out = torch.empty(S * m * 8, dtype=torch.uint8).pin_memory()
+    views = {d: h_out.view({"u64": torch.int64, "u32": torch.int32, "f64": torch.float64}[d])
+             for d in ("u64", "u32", "f64")}
+
+    def step():
+        for v, d in jobs():
+            ctx.fill_host(v, "jump", host_base[v], first, S, m, d, views[d])
+
+    step()  # warm-up: staging buffers are allocated on first use
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([el], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        el = float(tt.item())
+    h2d = sum(len(host_base[v]) for v, _ in jobs())
+    return {"value": world * bytes_per_step * args.e2e_steps / el / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": bytes_per_step,
+            "steps": args.e2e_steps, "ms_per_step": 1e3 * el / args.e2e_steps,
+            "api": "xr_fill_host (pinned host output, two staging buffers, copy/compute overlap)"}
+
+
+def run_profile(args):
+    """A small case for ncu: one warm-up launch, then --profile-launches launches
+    of the profiled kernel (fill: 2^16 streams x 2^10 outputs = 512 MiB of u64,
+    larger than L2; streams: jump-start of --profile-streams streams)."""
+    import torch
+    import paper_1805_01407_gb300 as xr
+    from paper_1805_01407_gb300 import build as libbuild
+    libbuild.build()
+    v = args.profile_variant
+    d = args.profile_dtype or W.native_dtype(v)
+    S, m = args.profile_streams, W.CONFIG_BULK["m"]
+    with xr.Context(0) as ctx:
+        base = ctx.empty_states(v, 1)
+        ctx.seed(v, W.CONFIG_BULK["seed"], base)
+        states = ctx.empty_states(v, S)
+        ctx.make_streams(v, "jump", base, 0, S, states)
+        out = ctx.empty_output(S * m, d) if args.profile == "fill" else None
+        for _ in range(1 + args.profile_launches):
+            if args.profile == "fill":
+                ctx.fill(v, states, S, m, d, out)
+            else:
+                ctx.make_streams(v, "jump", base, 0, S, states)
+        torch.cuda.synchronize()
+        assert ctx.status() == 0
+    print("profile case done: %s %s S=%d m=%d" % (args.profile, v, S, m))
+    return 0
+
+
+if __name__ == "__main__":
+    a = parse_args()
+    if a.profile:
+        sys.exit(run_profile(a))
+    sys.exit(run_reference(a) if a.impl == "reference" else run_xr(a))

@@ -1,0 +1,203 @@
+/*
+ * xr.h -- C ABI of libxr: bulk output generation from many independent
+ * scrambled linear generators on one GB300 GPU (sm_103a).
+ *
+ * The generators are those of Blackman & Vigna, "Scrambled Linear Pseudorandom
+ * Number Generators" (ACM TOMS; arXiv 1805.01407):
+ *   - linear engines xoshiro256 (Sec. 3.2, matrix S_4w, Table 4: A=17, B=45),
+ *     xoroshiro128 (Sec. 3.1, matrix X_2w, Table 4: (24,16,37), and (49,21,28)
+ *     for the ++ scrambler) and the 32-bit xoshiro128 (Table 7: A=9, B=11);
+ *   - scramblers + (Sec. 4.1), ++ (Sec. 4.3), ** (Sec. 4.4), parameters from
+ *     Tables 5 and 8; the output is computed from the current state before the
+ *     engine step (Sec. 2);
+ *   - seeding with SplitMix64 (Sec. 5.3);
+ *   - jumps: every engine is F2-linear, so advancing by J steps is the matrix
+ *     power T^J (Sec. 5, Sec. 6).  The paper prints no jump distances; this
+ *     library uses 2^(n/2) for a jump and 2^(3n/4) for a long jump of an n-bit
+ *     state (2^128 and 2^192 for xoshiro256, 2^64 and 2^96 otherwise);
+ *   - doubles in [0,1) from the upper 53 bits: (x >> 11) * 2^-53 (Sec. 5.3).
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are device memory owned by the caller (e.g. torch
+ *     tensors); h_* are host memory owned by the caller.  The library never
+ *     allocates or frees caller buffers.  The context owns its jump tables, a
+ *     status word and scratch for segment start states.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Every call that takes a stream only enqueues work on it and returns
+ *     without waiting, unless its comment says otherwise.
+ *   - A state is stored as its words in order, little-endian: 4 x uint64 (32 B)
+ *     for xoshiro256, 2 x uint64 (16 B) for xoroshiro128, 4 x uint32 (16 B) for
+ *     xoshiro128.  Arrays of states are contiguous, state i at byte i * state
+ *     bytes.  A state must not be all zero (captions of Figs. 1 and 3).
+ *   - Every call returns an xr status code.  Host-side argument errors return
+ *     XR_EINVAL before any work is enqueued.  A failed CUDA launch or copy
+ *     returns XR_ECUDA.  Errors found by kernels (an all-zero state) are
+ *     recorded in a sticky device status word read by xr_status().
+ *   - Device pointers must be aligned to the element size.  Output pointers
+ *     aligned to 16 bytes with rows (m * element bytes) a multiple of 16 bytes
+ *     take the fast path (TMA tile stores); other shapes take a plain-store
+ *     path that gives the same values more slowly.
+ */
+#ifndef XR_H
+#define XR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define XR_OK 0
+#define XR_EINVAL 1        /* bad argument (variant, dtype, size, pointer, kind) */
+#define XR_EZERO_STATE 2   /* an all-zero generator state was given or seen */
+#define XR_ENOMEM 3        /* the context could not allocate its own memory */
+#define XR_ECUDA 4         /* a CUDA call failed */
+#define XR_ETIMEOUT 5      /* a bounded device-side wait gave up */
+#define XR_EUNSUPPORTED 6  /* valid request this build does not implement */
+
+/* ---- enums ------------------------------------------------------------- */
+/* Generator = linear engine + scrambler (Tables 4, 5, 7, 8). */
+enum xr_variant {
+    XR_XOSHIRO256_PLUS = 0,       /* s0 + s3 */
+    XR_XOSHIRO256_PLUSPLUS = 1,   /* rotl(s0 + s3, 23) + s0 */
+    XR_XOSHIRO256_STARSTAR = 2,   /* rotl(s1 * 5, 7) * 9 */
+    XR_XOROSHIRO128_PLUS = 3,     /* s0 + s1, engine (24,16,37) */
+    XR_XOROSHIRO128_PLUSPLUS = 4, /* rotl(s0 + s1, 17) + s0, engine (49,21,28) */
+    XR_XOROSHIRO128_STARSTAR = 5, /* rotl(s0 * 5, 7) * 9, engine (24,16,37) */
+    XR_XOSHIRO128_PLUSPLUS = 6,   /* 32-bit: rotl(s0 + s3, 7) + s0 */
+    XR_XOSHIRO128_STARSTAR = 7,   /* 32-bit: rotl(s1 * 5, 7) * 9 */
+    XR_XOSHIRO128_PLUS = 8,       /* 32-bit: s0 + s3 */
+    XR_NUM_VARIANTS = 9
+};
+
+/* Value type of the outputs. */
+enum xr_dtype {
+    XR_U64 = 0,  /* raw 64-bit output; 64-bit generators only */
+    XR_U32 = 1,  /* raw 32-bit output; 32-bit generators only */
+    XR_F64 = 2,  /* double in [0,1): (x >> 11) * 2^-53, or x * 2^-32 for 32-bit words */
+    XR_F32 = 3   /* float in [0,1): upper 24 bits * 2^-24 */
+};
+
+/* Placement of the S x m outputs of xr_fill. */
+enum xr_layout {
+    XR_STREAM_MAJOR = 0, /* out[i * m + j] = output j of stream i */
+    XR_INTERLEAVED = 1   /* out[j * S + i] = output j of stream i */
+};
+
+enum xr_jump_kind {
+    XR_JUMP = 0,      /* advance 2^(n/2) steps */
+    XR_LONG_JUMP = 1  /* advance 2^(3n/4) steps */
+};
+
+typedef struct xr_ctx xr_ctx;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on `device` (made current on the calling thread).  Builds
+ * the jump tables T^(2^k), k = 0 .. n-1, of every engine on the device by
+ * stepping unit states (column j of T is the step of e_j, Sec. 3) and repeated
+ * squaring; waits for them.  About 3 MiB of device memory.  Returns
+ * XR_ENOMEM / XR_ECUDA on failure, with *out = NULL. */
+int xr_ctx_create(int device, xr_ctx **out);
+
+/* Free everything the context owns.  Waits for the device first.  NULL is
+ * accepted. */
+int xr_ctx_destroy(xr_ctx *ctx);
+
+/* ---- properties (pure host functions, no GPU needed) -------------------- */
+int xr_state_words(int variant);      /* 4, 2 or 4; -1 for a bad variant */
+int xr_word_bits(int variant);        /* 64 or 32; -1 for a bad variant */
+int xr_state_bytes(int variant);      /* 32 or 16; -1 for a bad variant */
+int xr_state_bits(int variant);       /* n = 256 or 128; -1 for a bad variant */
+int xr_dtype_bytes(int dtype);        /* 8, 4, 8, 4; -1 for a bad dtype */
+const char *xr_variant_name(int variant);  /* e.g. "xoshiro256**"; NULL if bad */
+const char *xr_error_string(int status);   /* never NULL */
+/* log2 of the jump distance of `kind` for `variant`; -1 if bad. */
+int xr_jump_log2(int variant, int kind);
+
+/* ---- seeding (Sec. 5.3) ---------------------------------------------------
+ * SplitMix64 initialized with the seed fills the state: consecutive 64-bit
+ * outputs for 64-bit words; for 32-bit words each output gives two words, low
+ * half first.  xr_seed writes one state to d_state; xr_seed_many writes
+ * count states, state i from d_seeds[i] (device array of uint64). */
+int xr_seed(xr_ctx *ctx, int variant, uint64_t seed, void *d_state, void *stream);
+int xr_seed_many(xr_ctx *ctx, int variant, const uint64_t *d_seeds, size_t count,
+                 void *d_states, void *stream);
+
+/* ---- state transfer ------------------------------------------------------
+ * xr_set_state copies one state from host words (h_words: state bytes, layout
+ * as above) to d_state; rejects the all-zero state with XR_EZERO_STATE.
+ * xr_get_state copies one state from d_state to h_words and waits on stream. */
+int xr_set_state(xr_ctx *ctx, int variant, const void *h_words, void *d_state, void *stream);
+int xr_get_state(xr_ctx *ctx, int variant, const void *d_state, void *h_words, void *stream);
+
+/* ---- jumps (Sec. 5, Sec. 6) ----------------------------------------------
+ * xr_jump: each of the `count` states in d_states is replaced by T^(times*J) s,
+ * the state after `times` successive jumps of the given kind.
+ * xr_advance: each state is replaced by T^nsteps s (nsteps next() calls).
+ * Both are F2 matrix-vector products with the powers T^(2^k) selected by the
+ * bits of the exponent. */
+int xr_jump(xr_ctx *ctx, int variant, int kind, void *d_states, size_t count, uint64_t times,
+            void *stream);
+int xr_advance(xr_ctx *ctx, int variant, void *d_states, size_t count, uint64_t nsteps,
+               void *stream);
+
+/* xr_make_streams: start states of S independent streams,
+ *   d_states_out[i] = J^(first + i)(d_base),  i = 0 .. S-1,
+ * where J is the jump (or long jump): stream 0 is the base after `first`
+ * jumps, each next stream one jump further.  d_base (one state) is read only;
+ * it may not overlap d_states_out. */
+int xr_make_streams(xr_ctx *ctx, int variant, int kind, const void *d_base, uint64_t first,
+                    size_t S, void *d_states_out, void *stream);
+
+/* ---- generation ------------------------------------------------------------
+ * xr_fill: S streams x m outputs.  Stream i starts at d_states[i] and emits
+ * m outputs of next() (scramble, then step), converted to dtype, placed by
+ * layout into d_out (S * m elements of dtype).  With write_back != 0 the
+ * state after the m steps is written back to d_states[i], so a later call
+ * continues each sequence.  S = 0 or m = 0 is a valid no-op (apart from
+ * write-back, which then leaves the states unchanged). */
+int xr_fill(xr_ctx *ctx, int variant, void *d_states, size_t S, size_t m, int dtype, int layout,
+            void *d_out, int write_back, void *stream);
+
+/* xr_fill_seq: the first n outputs of one sequence starting at d_state, into
+ * d_out (n elements of dtype); d_state is then advanced by n steps.  The
+ * sequence is split into segments of 2^10 outputs whose start states are
+ * T^(p * 2^10) s (jump-ahead), kept in the context's scratch memory, so the
+ * whole GPU works on one sequence.  Not safe to call concurrently on two
+ * streams with the same context (shared scratch). */
+int xr_fill_seq(xr_ctx *ctx, int variant, void *d_state, size_t n, int dtype, void *d_out,
+                void *stream);
+
+/* xr_fill_host: end-to-end call with host memory.  Copies one base state from
+ * h_base (host), makes S streams J^(first + i)(base), generates S x m outputs
+ * (stream-major) and copies them to h_out (host, S * m elements of dtype;
+ * page-locked memory gives full copy speed).  Generation and device-to-host
+ * copies overlap through two staging buffers the context owns.  Blocks until
+ * h_out is complete. */
+int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_base, uint64_t first,
+                 size_t S, size_t m, int dtype, void *h_out, void *stream);
+
+/* ---- status and inspection ------------------------------------------------ */
+
+/* Sticky device status: XR_OK, or the first error a kernel recorded
+ * (XR_EZERO_STATE).  Waits for the device.  reset != 0 clears it. */
+int xr_status(xr_ctx *ctx, int reset);
+
+/* Copy the jump table entry T^(2^k) of variant's engine to h_out (host):
+ * n columns, column c = T^(2^k) e_c as n/32 uint32 words (bit r of the column
+ * is bit r % 32 of word r / 32); n * n / 8 bytes.  Waits for the copy. */
+int xr_jump_table(xr_ctx *ctx, int variant, int k, void *h_out);
+
+/* Number of kernels this process has launched through libxr so far (all
+ * contexts; a host-side counter, no GPU needed).  Lets a caller count the
+ * launches inside a timed region. */
+uint64_t xr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XR_H */

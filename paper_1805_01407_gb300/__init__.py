@@ -1,0 +1,287 @@
+"""Bulk generation from scrambled linear pseudorandom generators on GB300.
+
+Thin Python binding of libxr (C ABI in include/xr.h).  Every computation runs
+in the library's CUDA kernels; this module only marshals torch tensors
+(device memory), CUDA streams and sizes into the C calls, checks that every
+buffer is large enough for the call, and turns status codes into exceptions.
+There is no CPU fallback: if libxr.so is missing the import of the native
+library fails loudly.
+
+Generators (Blackman & Vigna, arXiv 1805.01407): xoshiro256+/++/** and
+xoroshiro128+/++/** (64-bit words), xoshiro128++/**/+ (32-bit words).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = ["Context", "XRError", "VARIANTS", "DTYPES", "state_words", "word_bits", "state_bytes",
+           "state_bits", "jump_log2", "lib", "library_path"]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_PKG, "libxr.so")
+
+VARIANTS = {
+    "xoshiro256+": 0, "xoshiro256++": 1, "xoshiro256**": 2,
+    "xoroshiro128+": 3, "xoroshiro128++": 4, "xoroshiro128**": 5,
+    "xoshiro128++": 6, "xoshiro128**": 7, "xoshiro128+": 8,
+}
+DTYPES = {"u64": 0, "u32": 1, "f64": 2, "f32": 3}
+LAYOUTS = {"stream": 0, "interleaved": 1}
+KINDS = {"jump": 0, "long": 1}
+
+XR_OK, XR_EINVAL, XR_EZERO_STATE, XR_ENOMEM, XR_ECUDA, XR_ETIMEOUT, XR_EUNSUPPORTED = range(7)
+
+_lib = None
+
+
+class XRError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, _err(status), status))
+
+
+def _err(status):
+    return lib().xr_error_string(status).decode()
+
+
+def lib():
+    """The loaded libxr.so (built by __graft_entry__.build() or
+    `python -m paper_1805_01407_gb300.build`)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise ImportError("libxr.so is not built (%s); run `python -m paper_1805_01407_gb300.build`"
+                              % library_path)
+        L = ctypes.CDLL(library_path)
+        vp, sz, u64, i = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int
+        sigs = {
+            "xr_ctx_create": [i, ctypes.POINTER(vp)],
+            "xr_ctx_destroy": [vp],
+            "xr_state_words": [i], "xr_word_bits": [i], "xr_state_bytes": [i], "xr_state_bits": [i],
+            "xr_dtype_bytes": [i], "xr_variant_name": [i], "xr_error_string": [i],
+            "xr_jump_log2": [i, i],
+            "xr_seed": [vp, i, u64, vp, vp],
+            "xr_seed_many": [vp, i, vp, sz, vp, vp],
+            "xr_set_state": [vp, i, vp, vp, vp],
+            "xr_get_state": [vp, i, vp, vp, vp],
+            "xr_jump": [vp, i, i, vp, sz, u64, vp],
+            "xr_advance": [vp, i, vp, sz, u64, vp],
+            "xr_make_streams": [vp, i, i, vp, u64, sz, vp, vp],
+            "xr_fill": [vp, i, vp, sz, sz, i, i, vp, i, vp],
+            "xr_fill_seq": [vp, i, vp, sz, i, vp, vp],
+            "xr_fill_host": [vp, i, i, vp, u64, sz, sz, i, vp, vp],
+            "xr_status": [vp, i],
+            "xr_jump_table": [vp, i, i, vp],
+        }
+        L.xr_launch_count.argtypes = []
+        L.xr_launch_count.restype = ctypes.c_uint64
+        for name, args in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = i
+        L.xr_variant_name.restype = ctypes.c_char_p
+        L.xr_error_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _v(variant):
+    if isinstance(variant, str):
+        return VARIANTS[variant]
+    return int(variant)
+
+
+def state_words(variant):
+    return lib().xr_state_words(_v(variant))
+
+
+def word_bits(variant):
+    return lib().xr_word_bits(_v(variant))
+
+
+def state_bytes(variant):
+    return lib().xr_state_bytes(_v(variant))
+
+
+def state_bits(variant):
+    return lib().xr_state_bits(_v(variant))
+
+
+def jump_log2(variant, kind="jump"):
+    return lib().xr_jump_log2(_v(variant), KINDS[kind])
+
+
+def launch_count():
+    """Kernels launched through libxr by this process so far."""
+    return lib().xr_launch_count()
+
+
+def dtype_bytes(dtype):
+    return lib().xr_dtype_bytes(DTYPES[dtype])
+
+
+def native_dtype(variant):
+    return "u64" if word_bits(variant) == 64 else "u32"
+
+
+def _check(rc, what):
+    if rc != XR_OK:
+        raise XRError(rc, what)
+
+
+def _nbytes(t):
+    return t.numel() * t.element_size()
+
+
+def _need(t, nbytes, what):
+    """The tensor must be contiguous, on the GPU, and hold `nbytes`."""
+    if nbytes == 0:
+        return
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if _nbytes(t) < nbytes:
+        raise ValueError("%s holds %d bytes, the call needs %d" % (what, _nbytes(t), nbytes))
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def torch_dtype(dtype):
+    import torch
+    return {"u64": torch.int64, "u32": torch.int32, "f64": torch.float64, "f32": torch.float32}[dtype]
+
+
+class Context:
+    """A libxr context on one device: jump tables, status word, scratch.
+
+    Method names follow the C ABI (xr_seed -> seed, xr_fill -> fill, ...).
+    States are uint8/int32/int64 CUDA tensors holding `state_bytes(variant)`
+    bytes per state; outputs are CUDA tensors of the dtype's width (u64 as
+    torch.int64 bit patterns, u32 as torch.int32, f64, f32).
+    """
+
+    def __init__(self, device=0):
+        import torch
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        torch.cuda.set_device(self.device)
+        h = ctypes.c_void_p()
+        _check(lib().xr_ctx_create(self.device.index or 0, ctypes.byref(h)), "xr_ctx_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().xr_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -------------------------------------------------------------- helpers
+    def empty_states(self, variant, count):
+        import torch
+        return torch.zeros(count * state_bytes(variant), dtype=torch.uint8, device=self.device)
+
+    def empty_output(self, count, dtype):
+        import torch
+        return torch.empty(count, dtype=torch_dtype(dtype), device=self.device)
+
+    # -------------------------------------------------------------- C calls
+    def seed(self, variant, seed, d_state, stream=None):
+        _need(d_state, state_bytes(variant), "d_state")
+        _check(lib().xr_seed(self._h, _v(variant), seed & (2**64 - 1), d_state.data_ptr(),
+                             _stream(stream)), "xr_seed")
+
+    def seed_many(self, variant, d_seeds, d_states, stream=None):
+        count = d_seeds.numel()
+        _need(d_seeds, count * 8, "d_seeds")
+        _need(d_states, count * state_bytes(variant), "d_states")
+        _check(lib().xr_seed_many(self._h, _v(variant), d_seeds.data_ptr(), count,
+                                  d_states.data_ptr(), _stream(stream)), "xr_seed_many")
+
+    def set_state(self, variant, words, d_state, stream=None):
+        """words: bytes-like holding one state (little-endian words)."""
+        b = bytes(words)
+        if len(b) != state_bytes(variant):
+            raise ValueError("state must be %d bytes" % state_bytes(variant))
+        _need(d_state, len(b), "d_state")
+        buf = ctypes.create_string_buffer(b, len(b))
+        _check(lib().xr_set_state(self._h, _v(variant), buf, d_state.data_ptr(), _stream(stream)),
+               "xr_set_state")
+
+    def get_state(self, variant, d_state, stream=None) -> bytes:
+        n = state_bytes(variant)
+        _need(d_state, n, "d_state")
+        buf = ctypes.create_string_buffer(n)
+        _check(lib().xr_get_state(self._h, _v(variant), d_state.data_ptr(), buf, _stream(stream)),
+               "xr_get_state")
+        return buf.raw
+
+    def jump(self, variant, kind, d_states, count, times=1, stream=None):
+        _need(d_states, count * state_bytes(variant), "d_states")
+        _check(lib().xr_jump(self._h, _v(variant), KINDS[kind], d_states.data_ptr(), count, times,
+                             _stream(stream)), "xr_jump")
+
+    def advance(self, variant, d_states, count, nsteps, stream=None):
+        _need(d_states, count * state_bytes(variant), "d_states")
+        _check(lib().xr_advance(self._h, _v(variant), d_states.data_ptr(), count, nsteps,
+                                _stream(stream)), "xr_advance")
+
+    def make_streams(self, variant, kind, d_base, first, S, d_states_out, stream=None):
+        _need(d_base, state_bytes(variant), "d_base")
+        _need(d_states_out, S * state_bytes(variant), "d_states_out")
+        _check(lib().xr_make_streams(self._h, _v(variant), KINDS[kind], d_base.data_ptr(), first, S,
+                                     d_states_out.data_ptr(), _stream(stream)), "xr_make_streams")
+
+    def fill(self, variant, d_states, S, m, dtype, d_out, layout="stream", write_back=False,
+             stream=None):
+        _need(d_states, S * state_bytes(variant), "d_states")
+        _need(d_out, S * m * dtype_bytes(dtype), "d_out")
+        _check(lib().xr_fill(self._h, _v(variant), d_states.data_ptr(), S, m, DTYPES[dtype],
+                             LAYOUTS[layout], d_out.data_ptr(), int(bool(write_back)),
+                             _stream(stream)), "xr_fill")
+
+    def fill_seq(self, variant, d_state, n, dtype, d_out, stream=None):
+        _need(d_state, state_bytes(variant), "d_state")
+        _need(d_out, n * dtype_bytes(dtype), "d_out")
+        _check(lib().xr_fill_seq(self._h, _v(variant), d_state.data_ptr(), n, DTYPES[dtype],
+                                 d_out.data_ptr(), _stream(stream)), "xr_fill_seq")
+
+    def fill_host(self, variant, kind, base_words, first, S, m, dtype, h_out, stream=None):
+        """h_out: a CPU tensor (pinned for full speed) of >= S*m elements."""
+        b = bytes(base_words)
+        if len(b) != state_bytes(variant):
+            raise ValueError("state must be %d bytes" % state_bytes(variant))
+        if h_out.is_cuda or not h_out.is_contiguous() or _nbytes(h_out) < S * m * dtype_bytes(dtype):
+            raise ValueError("h_out must be a contiguous host tensor of S*m elements")
+        buf = ctypes.create_string_buffer(b, len(b))
+        _check(lib().xr_fill_host(self._h, _v(variant), KINDS[kind], buf, first, S, m, DTYPES[dtype],
+                                  h_out.data_ptr(), _stream(stream)), "xr_fill_host")
+
+    def status(self, reset=False):
+        return lib().xr_status(self._h, int(bool(reset)))
+
+    def jump_table(self, variant, k) -> bytes:
+        n = state_bits(variant)
+        buf = ctypes.create_string_buffer(n * n // 8)
+        _check(lib().xr_jump_table(self._h, _v(variant), k, buf), "xr_jump_table")
+        return buf.raw

@@ -1,0 +1,476 @@
+// xr_api.cu -- the C ABI of libxr (declared in include/xr.h): argument checks,
+// the context (jump tables, status word, scratch), and dispatch to kernels.
+#include <stdlib.h>
+#include <atomic>
+#include <string.h>
+
+#include "xr_device.cuh"
+#include "xr_internal.h"
+
+namespace xr {
+
+template <int V>
+cudaError_t launch_fill_v(int dtype, int layout, void *states, size_t S, size_t m, size_t ld,
+                          void *out, int write_back, int *status, cudaStream_t stream,
+                          EncodeTiledFn encode);
+extern template cudaError_t launch_fill_v<0>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
+extern template cudaError_t launch_fill_v<1>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
+extern template cudaError_t launch_fill_v<2>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
+extern template cudaError_t launch_fill_v<3>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
+extern template cudaError_t launch_fill_v<4>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
+extern template cudaError_t launch_fill_v<5>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
+extern template cudaError_t launch_fill_v<6>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
+extern template cudaError_t launch_fill_v<7>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
+extern template cudaError_t launch_fill_v<8>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
+
+static const int kEngineOf[XR_NUM_VARIANTS] = {ENG_XOSHIRO256, ENG_XOSHIRO256, ENG_XOSHIRO256,
+                                               ENG_XOROSHIRO128, ENG_XOROSHIRO128PP, ENG_XOROSHIRO128,
+                                               ENG_XOSHIRO128, ENG_XOSHIRO128, ENG_XOSHIRO128};
+static const int kEngineBits[NUM_ENGINES] = {256, 128, 128, 128};
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int engine_of(int variant) { return kEngineOf[variant]; }
+int engine_bits(int engine) { return kEngineBits[engine]; }
+
+cudaError_t launch_fill(int variant, int dtype, int layout, void *states, size_t S, size_t m,
+                        size_t ld, void *out, int write_back, int *status, cudaStream_t stream,
+                        EncodeTiledFn encode)
+{
+    switch (variant) {
+    case 0: return launch_fill_v<0>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 1: return launch_fill_v<1>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 2: return launch_fill_v<2>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 3: return launch_fill_v<3>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 4: return launch_fill_v<4>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 5: return launch_fill_v<5>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 6: return launch_fill_v<6>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 7: return launch_fill_v<7>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 8: return launch_fill_v<8>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace xr
+
+using namespace xr;
+
+// Segment length of xr_fill_seq: 2^SEQ_LOG2 outputs per segment.
+static const int SEQ_LOG2 = 10;
+// Largest staging buffer of xr_fill_host (two of them).
+static const size_t HOST_STAGING_BYTES = (size_t)256 << 20;
+
+struct xr_ctx {
+    int device;
+    uint32_t *tables[NUM_ENGINES];
+    int *d_status;
+    void *scratch;            // segment start states of xr_fill_seq
+    size_t scratch_bytes;
+    void *staging[2];         // output staging of xr_fill_host
+    void *chunk_states[2];    // stream start states of xr_fill_host
+    void *base_state;         // one state (xr_fill_host)
+    size_t staging_bytes, chunk_states_bytes;
+    cudaStream_t side;        // copy stream of xr_fill_host
+    cudaEvent_t ev_gen[2], ev_copy[2];
+    EncodeTiledFn encode;
+};
+
+static const char *kNames[XR_NUM_VARIANTS] = {
+    "xoshiro256+", "xoshiro256++", "xoshiro256**", "xoroshiro128+", "xoroshiro128++",
+    "xoroshiro128**", "xoshiro128++", "xoshiro128**", "xoshiro128+"};
+
+static bool variant_ok(int v) { return v >= 0 && v < XR_NUM_VARIANTS; }
+
+static int status_of(cudaError_t e)
+{
+    if (e == cudaSuccess) return XR_OK;
+    if (e == cudaErrorMemoryAllocation) return XR_ENOMEM;
+    if (e == cudaErrorInvalidValue) return XR_EINVAL;
+    return XR_ECUDA;
+}
+
+// ---------------------------------------------------------------- properties
+
+extern "C" uint64_t xr_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" int xr_state_words(int variant)
+{
+    if (!variant_ok(variant)) return -1;
+    return engine_of(variant) == ENG_XOSHIRO256 || engine_of(variant) == ENG_XOSHIRO128 ? 4 : 2;
+}
+
+extern "C" int xr_word_bits(int variant)
+{
+    if (!variant_ok(variant)) return -1;
+    return engine_of(variant) == ENG_XOSHIRO128 ? 32 : 64;
+}
+
+extern "C" int xr_state_bytes(int variant)
+{
+    if (!variant_ok(variant)) return -1;
+    return xr_state_words(variant) * xr_word_bits(variant) / 8;
+}
+
+extern "C" int xr_state_bits(int variant)
+{
+    if (!variant_ok(variant)) return -1;
+    return engine_bits(engine_of(variant));
+}
+
+extern "C" int xr_dtype_bytes(int dtype)
+{
+    switch (dtype) {
+    case XR_U64: case XR_F64: return 8;
+    case XR_U32: case XR_F32: return 4;
+    default: return -1;
+    }
+}
+
+extern "C" const char *xr_variant_name(int variant)
+{
+    return variant_ok(variant) ? kNames[variant] : NULL;
+}
+
+extern "C" const char *xr_error_string(int status)
+{
+    switch (status) {
+    case XR_OK: return "ok";
+    case XR_EINVAL: return "invalid argument";
+    case XR_EZERO_STATE: return "all-zero generator state";
+    case XR_ENOMEM: return "out of device memory";
+    case XR_ECUDA: return "CUDA error";
+    case XR_ETIMEOUT: return "device-side wait timed out";
+    case XR_EUNSUPPORTED: return "not supported";
+    default: return "unknown status";
+    }
+}
+
+extern "C" int xr_jump_log2(int variant, int kind)
+{
+    if (!variant_ok(variant)) return -1;
+    const int n = xr_state_bits(variant);
+    if (kind == XR_JUMP) return n / 2;
+    if (kind == XR_LONG_JUMP) return 3 * n / 4;
+    return -1;
+}
+
+static bool dtype_ok(int variant, int dtype)
+{
+    if (dtype == XR_F64 || dtype == XR_F32) return true;
+    if (dtype == XR_U64) return xr_word_bits(variant) == 64;
+    if (dtype == XR_U32) return xr_word_bits(variant) == 32;
+    return false;
+}
+
+// ---------------------------------------------------------------- context
+
+extern "C" int xr_ctx_destroy(xr_ctx *ctx)
+{
+    if (!ctx) return XR_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (int e = 0; e < NUM_ENGINES; ++e) cudaFree(ctx->tables[e]);
+    cudaFree(ctx->d_status);
+    cudaFree(ctx->scratch);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(ctx->staging[b]);
+        cudaFree(ctx->chunk_states[b]);
+        if (ctx->ev_gen[b]) cudaEventDestroy(ctx->ev_gen[b]);
+        if (ctx->ev_copy[b]) cudaEventDestroy(ctx->ev_copy[b]);
+    }
+    cudaFree(ctx->base_state);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    free(ctx);
+    return XR_OK;
+}
+
+extern "C" int xr_ctx_create(int device, xr_ctx **out)
+{
+    if (!out) return XR_EINVAL;
+    *out = NULL;
+    if (cudaSetDevice(device) != cudaSuccess) return XR_ECUDA;
+    xr_ctx *ctx = (xr_ctx *)calloc(1, sizeof(xr_ctx));
+    if (!ctx) return XR_ENOMEM;
+    ctx->device = device;
+    cudaDriverEntryPointQueryResult q;
+    void *fn = NULL;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        ctx->encode = (EncodeTiledFn)fn;
+    cudaGetLastError();
+    int rc = XR_OK;
+    for (int e = 0; e < NUM_ENGINES && rc == XR_OK; ++e) {
+        const size_t n = (size_t)engine_bits(e);
+        rc = status_of(cudaMalloc((void **)&ctx->tables[e], n * n * n / 8));
+        if (rc == XR_OK) rc = status_of(launch_build_tables(e, ctx->tables[e], 0));
+    }
+    if (rc == XR_OK) rc = status_of(cudaMalloc((void **)&ctx->d_status, sizeof(int)));
+    if (rc == XR_OK) rc = status_of(cudaMemset(ctx->d_status, 0, sizeof(int)));
+    if (rc == XR_OK) rc = status_of(cudaMalloc(&ctx->base_state, 32));
+    if (rc == XR_OK) rc = status_of(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    for (int b = 0; b < 2 && rc == XR_OK; ++b) {
+        rc = status_of(cudaEventCreateWithFlags(&ctx->ev_gen[b], cudaEventDisableTiming));
+        if (rc == XR_OK) rc = status_of(cudaEventCreateWithFlags(&ctx->ev_copy[b], cudaEventDisableTiming));
+    }
+    if (rc == XR_OK) rc = status_of(cudaDeviceSynchronize());
+    if (rc != XR_OK) {
+        xr_ctx_destroy(ctx);
+        return rc == XR_EINVAL ? XR_ECUDA : rc;
+    }
+    *out = ctx;
+    return XR_OK;
+}
+
+extern "C" int xr_status(xr_ctx *ctx, int reset)
+{
+    if (!ctx) return XR_EINVAL;
+    int h = 0;
+    if (cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return XR_ECUDA;
+    if (reset && cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) return XR_ECUDA;
+    return h;
+}
+
+extern "C" int xr_jump_table(xr_ctx *ctx, int variant, int k, void *h_out)
+{
+    if (!ctx || !variant_ok(variant) || !h_out) return XR_EINVAL;
+    const int e = engine_of(variant);
+    const size_t n = (size_t)engine_bits(e);
+    if (k < 0 || (size_t)k >= n) return XR_EINVAL;
+    const size_t bytes = n * n / 8;
+    return status_of(cudaMemcpy(h_out, (const char *)ctx->tables[e] + (size_t)k * bytes, bytes,
+                                cudaMemcpyDeviceToHost));
+}
+
+// ---------------------------------------------------------------- seeding, states
+
+extern "C" int xr_seed(xr_ctx *ctx, int variant, uint64_t seed, void *d_state, void *stream)
+{
+    if (!ctx || !variant_ok(variant) || !d_state || ((uintptr_t)d_state % 16)) return XR_EINVAL;
+    return status_of(launch_seed(variant, NULL, seed, 1, d_state, ctx->d_status, (cudaStream_t)stream));
+}
+
+extern "C" int xr_seed_many(xr_ctx *ctx, int variant, const uint64_t *d_seeds, size_t count,
+                            void *d_states, void *stream)
+{
+    if (!ctx || !variant_ok(variant)) return XR_EINVAL;
+    if (count == 0) return XR_OK;
+    if (!d_seeds || !d_states || ((uintptr_t)d_states % 16) || ((uintptr_t)d_seeds % 8))
+        return XR_EINVAL;
+    return status_of(launch_seed(variant, d_seeds, 0, count, d_states, ctx->d_status, (cudaStream_t)stream));
+}
+
+extern "C" int xr_set_state(xr_ctx *ctx, int variant, const void *h_words, void *d_state, void *stream)
+{
+    if (!ctx || !variant_ok(variant) || !h_words || !d_state) return XR_EINVAL;
+    const int nb = xr_state_bytes(variant);
+    unsigned char any = 0;
+    for (int b = 0; b < nb; ++b) any |= ((const unsigned char *)h_words)[b];
+    if (!any) return XR_EZERO_STATE;
+    return status_of(cudaMemcpyAsync(d_state, h_words, (size_t)nb, cudaMemcpyHostToDevice,
+                                     (cudaStream_t)stream));
+}
+
+extern "C" int xr_get_state(xr_ctx *ctx, int variant, const void *d_state, void *h_words, void *stream)
+{
+    if (!ctx || !variant_ok(variant) || !h_words || !d_state) return XR_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(h_words, d_state, (size_t)xr_state_bytes(variant),
+                                    cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return status_of(e);
+}
+
+// ---------------------------------------------------------------- jumps
+
+// Matrix indices k = (d + b) mod n for the set bits b of e.
+static KList klist(uint64_t e, int d, int n)
+{
+    KList ks;
+    ks.n = 0;
+    for (int b = 0; b < 64; ++b)
+        if ((e >> b) & 1u) ks.k[ks.n++] = (d + b) % n;
+    return ks;
+}
+
+static bool states_ok(const void *p) { return p && ((uintptr_t)p % 16) == 0; }
+
+extern "C" int xr_jump(xr_ctx *ctx, int variant, int kind, void *d_states, size_t count,
+                       uint64_t times, void *stream)
+{
+    if (!ctx || !variant_ok(variant) || (kind != XR_JUMP && kind != XR_LONG_JUMP)) return XR_EINVAL;
+    if (count == 0 || times == 0) return XR_OK;
+    if (!states_ok(d_states)) return XR_EINVAL;
+    const int e = engine_of(variant);
+    return status_of(launch_apply_pow(e, ctx->tables[e], klist(times, xr_jump_log2(variant, kind), engine_bits(e)),
+                                      d_states, count, (cudaStream_t)stream));
+}
+
+extern "C" int xr_advance(xr_ctx *ctx, int variant, void *d_states, size_t count, uint64_t nsteps,
+                          void *stream)
+{
+    if (!ctx || !variant_ok(variant)) return XR_EINVAL;
+    if (count == 0 || nsteps == 0) return XR_OK;
+    if (!states_ok(d_states)) return XR_EINVAL;
+    const int e = engine_of(variant);
+    return status_of(launch_apply_pow(e, ctx->tables[e], klist(nsteps, 0, engine_bits(e)), d_states,
+                                      count, (cudaStream_t)stream));
+}
+
+// out[i] = (T^(2^d))^(first + i) base for i < S.
+static cudaError_t make_streams(xr_ctx *ctx, int variant, int d, const void *d_base, uint64_t first,
+                                size_t S, void *out, cudaStream_t st)
+{
+    if (S == 0) return cudaSuccess;
+    const int e = engine_of(variant);
+    cudaError_t err = cudaMemcpyAsync(out, d_base, (size_t)xr_state_bytes(variant),
+                                      cudaMemcpyDeviceToDevice, st);
+    if (err != cudaSuccess) return err;
+    if (first) {
+        err = launch_apply_pow(e, ctx->tables[e], klist(first, d, engine_bits(e)), out, 1, st);
+        if (err != cudaSuccess) return err;
+    }
+    return launch_tree(e, ctx->tables[e], d, out, S, st);
+}
+
+extern "C" int xr_make_streams(xr_ctx *ctx, int variant, int kind, const void *d_base, uint64_t first,
+                               size_t S, void *d_states_out, void *stream)
+{
+    if (!ctx || !variant_ok(variant) || (kind != XR_JUMP && kind != XR_LONG_JUMP)) return XR_EINVAL;
+    if (S == 0) return XR_OK;
+    if (!states_ok(d_base) || !states_ok(d_states_out)) return XR_EINVAL;
+    const size_t sb = (size_t)xr_state_bytes(variant);
+    const char *b = (const char *)d_base, *o = (const char *)d_states_out;
+    if (b < o + S * sb && o < b + sb) return XR_EINVAL;  // overlap
+    return status_of(make_streams(ctx, variant, xr_jump_log2(variant, kind), d_base, first, S,
+                                  d_states_out, (cudaStream_t)stream));
+}
+
+// ---------------------------------------------------------------- generation
+
+static int fill_args_ok(int variant, void *d_states, size_t S, size_t m, int dtype, int layout, void *d_out)
+{
+    if (!variant_ok(variant) || !dtype_ok(variant, dtype)) return 0;
+    if (layout != XR_STREAM_MAJOR && layout != XR_INTERLEAVED) return 0;
+    if (S == 0) return 1;
+    if (!states_ok(d_states)) return 0;
+    if (m == 0) return 1;
+    const size_t es = (size_t)xr_dtype_bytes(dtype);
+    if (!d_out || ((uintptr_t)d_out % es)) return 0;
+    if (m > (SIZE_MAX / es) / S) return 0;
+    return 1;
+}
+
+extern "C" int xr_fill(xr_ctx *ctx, int variant, void *d_states, size_t S, size_t m, int dtype,
+                       int layout, void *d_out, int write_back, void *stream)
+{
+    if (!ctx || !fill_args_ok(variant, d_states, S, m, dtype, layout, d_out)) return XR_EINVAL;
+    if (S == 0 || m == 0) return XR_OK;
+    return status_of(launch_fill(variant, dtype, layout, d_states, S, m, m, d_out, write_back,
+                                 ctx->d_status, (cudaStream_t)stream, ctx->encode));
+}
+
+static cudaError_t ensure(void **p, size_t *have, size_t want)
+{
+    if (*have >= want && *p) return cudaSuccess;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    cudaFree(*p);
+    *p = NULL;
+    *have = 0;
+    e = cudaMalloc(p, want);
+    if (e == cudaSuccess) *have = want;
+    return e;
+}
+
+extern "C" int xr_fill_seq(xr_ctx *ctx, int variant, void *d_state, size_t n, int dtype, void *d_out,
+                           void *stream)
+{
+    if (!ctx || !variant_ok(variant) || !dtype_ok(variant, dtype)) return XR_EINVAL;
+    if (n == 0) return XR_OK;
+    const size_t es = (size_t)xr_dtype_bytes(dtype);
+    if (!states_ok(d_state) || !d_out || ((uintptr_t)d_out % es)) return XR_EINVAL;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const size_t seg = (size_t)1 << SEQ_LOG2;
+    const size_t full = n / seg, tail = n % seg, P = full + (tail ? 1 : 0);
+    const size_t sb = (size_t)xr_state_bytes(variant);
+    size_t cap = ctx->scratch_bytes;
+    cudaError_t err = ensure(&ctx->scratch, &cap, P * sb);
+    ctx->scratch_bytes = cap;
+    if (err != cudaSuccess) return status_of(err);
+    // segment p starts at T^(p * 2^SEQ_LOG2) s
+    err = make_streams(ctx, variant, SEQ_LOG2, d_state, 0, P, ctx->scratch, st);
+    if (err == cudaSuccess && full)
+        err = launch_fill(variant, dtype, XR_STREAM_MAJOR, ctx->scratch, full, seg, seg, d_out, 1,
+                          ctx->d_status, st, ctx->encode);
+    if (err == cudaSuccess && tail)
+        err = launch_fill(variant, dtype, XR_STREAM_MAJOR, (char *)ctx->scratch + full * sb, 1, tail,
+                          seg, (char *)d_out + full * seg * es, 1, ctx->d_status, st, ctx->encode);
+    // the last segment's written-back state is T^n s
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(d_state, (char *)ctx->scratch + (P - 1) * sb, sb,
+                              cudaMemcpyDeviceToDevice, st);
+    return status_of(err);
+}
+
+extern "C" int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_base, uint64_t first,
+                            size_t S, size_t m, int dtype, void *h_out, void *stream)
+{
+    if (!ctx || !variant_ok(variant) || !dtype_ok(variant, dtype) || !h_base) return XR_EINVAL;
+    if (kind != XR_JUMP && kind != XR_LONG_JUMP) return XR_EINVAL;
+    if (S == 0 || m == 0) return XR_OK;
+    if (!h_out) return XR_EINVAL;
+    const size_t es = (size_t)xr_dtype_bytes(dtype);
+    if (m > (SIZE_MAX / es) / S) return XR_EINVAL;
+    const size_t sb = (size_t)xr_state_bytes(variant);
+    unsigned char any = 0;
+    for (size_t b = 0; b < sb; ++b) any |= ((const unsigned char *)h_base)[b];
+    if (!any) return XR_EZERO_STATE;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const size_t row = m * es;
+    size_t ch = HOST_STAGING_BYTES / row;
+    if (ch == 0) ch = 1;
+    if (ch > S) ch = S;
+    cudaError_t err = cudaSuccess;
+    if (ctx->staging_bytes < ch * row || ctx->chunk_states_bytes < ch * sb) {
+        err = cudaDeviceSynchronize();
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(ctx->staging[b]);
+            cudaFree(ctx->chunk_states[b]);
+            ctx->staging[b] = ctx->chunk_states[b] = NULL;
+        }
+        ctx->staging_bytes = ctx->chunk_states_bytes = 0;
+        for (int b = 0; b < 2 && err == cudaSuccess; ++b) {
+            err = cudaMalloc(&ctx->staging[b], ch * row);
+            if (err == cudaSuccess) err = cudaMalloc(&ctx->chunk_states[b], ch * sb);
+        }
+        if (err != cudaSuccess) return status_of(err);
+        ctx->staging_bytes = ch * row;
+        ctx->chunk_states_bytes = ch * sb;
+    }
+    const int d = xr_jump_log2(variant, kind);
+    err = cudaMemcpyAsync(ctx->base_state, h_base, sb, cudaMemcpyHostToDevice, st);
+    size_t c = 0;
+    for (size_t s0 = 0; s0 < S && err == cudaSuccess; s0 += ch, ++c) {
+        const int b = (int)(c & 1);
+        const size_t cnt = (S - s0) < ch ? (S - s0) : ch;
+        if (c >= 2) err = cudaStreamWaitEvent(st, ctx->ev_copy[b], 0);
+        if (err == cudaSuccess)
+            err = make_streams(ctx, variant, d, ctx->base_state, first + s0, cnt, ctx->chunk_states[b], st);
+        if (err == cudaSuccess)
+            err = launch_fill(variant, dtype, XR_STREAM_MAJOR, ctx->chunk_states[b], cnt, m, m,
+                              ctx->staging[b], 0, ctx->d_status, st, ctx->encode);
+        if (err == cudaSuccess) err = cudaEventRecord(ctx->ev_gen[b], st);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(ctx->side, ctx->ev_gen[b], 0);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync((char *)h_out + s0 * row, ctx->staging[b], cnt * row,
+                                  cudaMemcpyDeviceToHost, ctx->side);
+        if (err == cudaSuccess) err = cudaEventRecord(ctx->ev_copy[b], ctx->side);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(ctx->side);
+    cudaError_t e3 = cudaStreamSynchronize(st);
+    if (err == cudaSuccess) err = e2;
+    if (err == cudaSuccess) err = e3;
+    return status_of(err);
+}

@@ -1,0 +1,286 @@
+// xr_device.cuh -- device-side building blocks of libxr (sm_103a).
+//
+// Linear engines (Sec. 3), scramblers (Sec. 4), exact output conversions
+// (Sec. 5.3), F2 matrix-vector products for jumps (Sec. 5, 6), and inline-PTX
+// wrappers for the Blackwell bulk-tensor (TMA) stores used by the fill kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace xr {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// ---------------------------------------------------------------- word ops
+__device__ __forceinline__ u64 rotl(u64 x, int r) { return (x << r) | (x >> (64 - r)); }
+__device__ __forceinline__ u32 rotl(u32 x, int r) { return __funnelshift_l(x, x, r); }
+
+// ---------------------------------------------------------------- engines
+// xoshiro with four words (Sec. 3.2): the new words are the columns of S_4w,
+//   s0' = s0 ^ s1 ^ s3          s1' = s0 ^ s1 ^ s2
+//   s2' = s0 ^ s2 ^ (s1 << A)   s3' = rotl(s1 ^ s3, B)
+template <typename W, int A, int B>
+struct Xoshiro4 {
+    typedef W word;
+    static constexpr int K = 4;
+    static constexpr int NBITS = 4 * 8 * (int)sizeof(W);
+    W s[4];
+    __device__ __forceinline__ void step()
+    {
+        const W x02 = s[0] ^ s[2];
+        const W x13 = s[1] ^ s[3];
+        const W n2 = x02 ^ (s[1] << A);
+        s[1] = s[1] ^ x02;
+        s[0] = s[0] ^ x13;
+        s[2] = n2;
+        s[3] = rotl(x13, B);
+    }
+};
+
+// xoroshiro with two words (Sec. 3.1), the columns of X_2w:
+//   t = s0 ^ s1;  s0' = rotl(s0, A) ^ t ^ (t << B);  s1' = rotl(t, C)
+template <typename W, int A, int B, int C>
+struct Xoroshiro2 {
+    typedef W word;
+    static constexpr int K = 2;
+    static constexpr int NBITS = 2 * 8 * (int)sizeof(W);
+    W s[2];
+    __device__ __forceinline__ void step()
+    {
+        const W t = s[0] ^ s[1];
+        s[0] = rotl(s[0], A) ^ t ^ (t << B);
+        s[1] = rotl(t, C);
+    }
+};
+
+// Engine ids used for the jump tables.
+enum { ENG_XOSHIRO256 = 0, ENG_XOROSHIRO128 = 1, ENG_XOROSHIRO128PP = 2, ENG_XOSHIRO128 = 3,
+       NUM_ENGINES = 4 };
+
+template <int ENG> struct EngineOf;
+template <> struct EngineOf<ENG_XOSHIRO256> { typedef Xoshiro4<u64, 17, 45> type; };      // Table 4
+template <> struct EngineOf<ENG_XOROSHIRO128> { typedef Xoroshiro2<u64, 24, 16, 37> type; };  // Table 4
+template <> struct EngineOf<ENG_XOROSHIRO128PP> { typedef Xoroshiro2<u64, 49, 21, 28> type; };// Table 4
+template <> struct EngineOf<ENG_XOSHIRO128> { typedef Xoshiro4<u32, 9, 11> type; };        // Table 7
+
+// ---------------------------------------------------------------- generators
+// Scrambler applied to the current state (Sec. 2), parameters of Tables 5, 8.
+template <int V> struct Gen;
+
+#define XR_GEN(V, ENG, BODY)                                                    \
+    template <> struct Gen<V> {                                                 \
+        static constexpr int engine = ENG;                                      \
+        typedef typename EngineOf<ENG>::type E;                                 \
+        typedef typename E::word word;                                          \
+        __device__ __forceinline__ static word out(const E &e) { BODY }         \
+    };
+
+XR_GEN(0, ENG_XOSHIRO256, return e.s[0] + e.s[3];)                              // xoshiro256+
+XR_GEN(1, ENG_XOSHIRO256, return rotl(e.s[0] + e.s[3], 23) + e.s[0];)          // xoshiro256++
+XR_GEN(2, ENG_XOSHIRO256, return rotl(e.s[1] * 5ull, 7) * 9ull;)               // xoshiro256**
+XR_GEN(3, ENG_XOROSHIRO128, return e.s[0] + e.s[1];)                            // xoroshiro128+
+XR_GEN(4, ENG_XOROSHIRO128PP, return rotl(e.s[0] + e.s[1], 17) + e.s[0];)      // xoroshiro128++
+XR_GEN(5, ENG_XOROSHIRO128, return rotl(e.s[0] * 5ull, 7) * 9ull;)             // xoroshiro128**
+XR_GEN(6, ENG_XOSHIRO128, return rotl(e.s[0] + e.s[3], 7) + e.s[0];)           // xoshiro128++
+XR_GEN(7, ENG_XOSHIRO128, return rotl(e.s[1] * 5u, 7) * 9u;)                   // xoshiro128**
+XR_GEN(8, ENG_XOSHIRO128, return e.s[0] + e.s[3];)                              // xoshiro128+
+#undef XR_GEN
+
+// ---------------------------------------------------------------- state I/O
+// A state in memory is its words in order, little-endian; 32 B or 16 B.
+template <typename E>
+__device__ __forceinline__ void load_state(E &e, const void *p)
+{
+    if (sizeof(e.s) == 32) {
+        const uint4 a = reinterpret_cast<const uint4 *>(p)[0];
+        const uint4 b = reinterpret_cast<const uint4 *>(p)[1];
+        u64 *w = reinterpret_cast<u64 *>(&e.s[0]);
+        w[0] = (u64)a.x | ((u64)a.y << 32); w[1] = (u64)a.z | ((u64)a.w << 32);
+        w[2] = (u64)b.x | ((u64)b.y << 32); w[3] = (u64)b.z | ((u64)b.w << 32);
+    } else {
+        const uint4 a = reinterpret_cast<const uint4 *>(p)[0];
+        u32 *w = reinterpret_cast<u32 *>(&e.s[0]);
+        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    }
+}
+
+template <typename E>
+__device__ __forceinline__ void store_state(const E &e, void *p)
+{
+    const u32 *w = reinterpret_cast<const u32 *>(&e.s[0]);
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+    q[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    if (sizeof(e.s) == 32) q[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// State <-> its n / 32 little-endian u32 words held in registers.
+template <typename E, int NW>
+__device__ __forceinline__ void from_words(E &e, const u32 (&w)[NW])
+{
+    if constexpr (sizeof(typename E::word) == 8) {
+#pragma unroll
+        for (int j = 0; j < E::K; ++j) e.s[j] = (u64)w[2 * j] | ((u64)w[2 * j + 1] << 32);
+    } else {
+#pragma unroll
+        for (int j = 0; j < E::K; ++j) e.s[j] = w[j];
+    }
+}
+
+template <typename E, int NW>
+__device__ __forceinline__ void to_words(const E &e, u32 (&w)[NW])
+{
+    if constexpr (sizeof(typename E::word) == 8) {
+#pragma unroll
+        for (int j = 0; j < E::K; ++j) {
+            w[2 * j] = (u32)e.s[j];
+            w[2 * j + 1] = (u32)(e.s[j] >> 32);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < E::K; ++j) w[j] = e.s[j];
+    }
+}
+
+template <typename E>
+__device__ __forceinline__ bool state_is_zero(const E &e)
+{
+    typename E::word acc = 0;
+#pragma unroll
+    for (int j = 0; j < E::K; ++j) acc |= e.s[j];
+    return acc == 0;
+}
+
+// ---------------------------------------------------------------- conversions
+// Output element codes (match xr_dtype).
+enum { DT_U64 = 0, DT_U32 = 1, DT_F64 = 2, DT_F32 = 3 };
+
+// (x >> 11) * 2^-53 as binary64 bits, built with integer operations only.  With
+// v = x >> 11 != 0 and lz = clz64(v) (11 <= lz <= 63), the leading one of v is
+// bit p = 63 - lz, the value is 1.f * 2^(p - 53), so the biased exponent is
+// p + 970 and the fraction is v << (52 - p) without its leading one.  Adding
+// the shifted v (whose leading one lands on bit 52) to (p + 969) << 52 sets both
+// at once: bits = (v << (lz - 11)) + ((1032 - lz) << 52).  v = 0 gives +0.0.
+__device__ __forceinline__ u64 unit_f64_bits(u64 x)
+{
+    const u64 v = x >> 11;
+    const int lz = __clzll(v);
+    const u64 bits = (v << (lz - 11)) + ((u64)(1032 - lz) << 52);
+    return v ? bits : 0ull;
+}
+
+// x * 2^-32 as binary64 bits for a 32-bit word: leading one at bit p = 31 - lz,
+// value 1.f * 2^(p - 32), biased exponent p + 991:
+// bits = (x << (21 + lz)) + ((1021 - lz) << 52).
+__device__ __forceinline__ u64 unit_f64_bits(u32 x)
+{
+    const int lz = __clz(x);
+    const u64 bits = ((u64)x << ((21 + lz) & 63)) + ((u64)(1021 - lz) << 52);
+    return x ? bits : 0ull;
+}
+
+// Upper 24 bits times 2^-24 as binary32 bits (exact: a 24-bit integer converts
+// exactly and the scaling is a power of two).
+__device__ __forceinline__ u32 unit_f32_bits(u64 x) { return __float_as_uint(__uint2float_rn((u32)(x >> 40)) * 0x1p-24f); }
+__device__ __forceinline__ u32 unit_f32_bits(u32 x) { return __float_as_uint(__uint2float_rn(x >> 8) * 0x1p-24f); }
+
+template <int DT> struct OutElem { typedef u64 type; };
+template <> struct OutElem<DT_U32> { typedef u32 type; };
+template <> struct OutElem<DT_F32> { typedef u32 type; };
+
+template <int DT, typename W>
+__device__ __forceinline__ typename OutElem<DT>::type convert(W x)
+{
+    if (DT == DT_U64 || DT == DT_U32) return (typename OutElem<DT>::type)x;
+    if (DT == DT_F64) return (typename OutElem<DT>::type)unit_f64_bits(x);
+    return (typename OutElem<DT>::type)unit_f32_bits(x);
+}
+
+// ---------------------------------------------------------------- F2 algebra
+// A state is a column vector of n bits; bit c is bit c % 32 of u32 word c / 32
+// of the state in memory.  A matrix is stored by columns: column c (the image
+// of the unit state e_c) is NW = n / 32 consecutive u32 words.
+//
+// r = M v as the XOR of the columns selected by the set bits of v.  Every
+// thread of a warp walks the columns in the same order, so the column loads are
+// warp-uniform (one broadcast per load) whatever the vectors are.
+template <int NW, bool SHARED>
+__device__ __forceinline__ void f2_matvec(const u32 *__restrict__ M, const u32 (&v)[NW],
+                                          u32 (&r)[NW])
+{
+    u32 acc[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) acc[w] = 0u;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const u32 bits = v[w];
+#pragma unroll 8
+        for (int b = 0; b < 32; ++b) {
+            const u32 mask = (u32)((int)(bits << (31 - b)) >> 31);
+            const uint4 *col = reinterpret_cast<const uint4 *>(M + (size_t)(w * 32 + b) * NW);
+#pragma unroll
+            for (int q = 0; q < NW / 4; ++q) {
+                uint4 c;
+                if (SHARED) c = col[q];
+                else c = __ldg(col + q);
+                acc[4 * q + 0] ^= c.x & mask;
+                acc[4 * q + 1] ^= c.y & mask;
+                acc[4 * q + 2] ^= c.z & mask;
+                acc[4 * q + 3] ^= c.w & mask;
+            }
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < NW; ++w) r[w] = acc[w];
+}
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ u32 smem_addr(const void *p)
+{
+    return (u32)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void st_shared_v4(u32 addr, u32 a, u32 b, u32 c, u32 d)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+                 "r"(d)
+                 : "memory");
+}
+
+// Order this thread's generic-proxy shared-memory writes before later
+// async-proxy (TMA) reads of the same memory.
+__device__ __forceinline__ void fence_proxy_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 2D tile store shared -> global through the tensor map (cp.async.bulk.tensor).
+// Elements outside the tensor's extent are not written.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, u32 src, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(src), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Wait until at most N committed bulk groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+// Wait until at most N committed bulk groups are still in flight (writes done).
+template <int N>
+__device__ __forceinline__ void bulk_wait_all()
+{
+    asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
+}  // namespace xr

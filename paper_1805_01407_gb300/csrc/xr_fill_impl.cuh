@@ -1,0 +1,298 @@
+// xr_fill_impl.cuh -- bulk generation kernels (engine step + scrambler +
+// conversion + store), instantiated per generator by xr_fill_*.cu.
+//
+// One thread owns one stream: its state stays in registers for the whole call
+// and it emits the stream's outputs in order (next() = scramble the current
+// state, then step; Sec. 2).  Stream-major output (out[i * ld + j]) makes each
+// thread write its own row, so rows are staged per warp in shared memory as a
+// 32-row x 128-byte tile in the 128-byte swizzled layout and written by one
+// TMA tile store (cp.async.bulk.tensor.2d) per tile; two tiles per warp let
+// the warp generate the next tile while the previous one drains.  Rows and
+// columns past the tensor's extent are clipped by the TMA unit, so ragged S
+// and m need no extra code.  Output shapes TMA cannot describe take the
+// plain-store path (same staging, then warp-wide stores); the interleaved
+// layout (out[j * S + i]) is already coalesced and stores directly.
+#pragma once
+
+#include "xr_device.cuh"
+#include "xr_internal.h"
+
+namespace xr {
+
+constexpr int FILL_WARPS = 4;          // warps per CTA
+constexpr int FILL_NBUF = 2;           // shared-memory tiles per warp
+constexpr int TILE_BYTES = 32 * 128;   // 32 rows x 128 bytes
+constexpr int FILL_SMEM = FILL_WARPS * FILL_NBUF * TILE_BYTES + 1024;  // + alignment slack
+
+// Next 16 bytes of output elements (2 x 8 B or 4 x 4 B), stepping the engine.
+template <typename G, int DT>
+__device__ __forceinline__ void gen16(typename G::E &e, u32 (&w)[4])
+{
+    typedef typename OutElem<DT>::type OT;
+    if (sizeof(OT) == 8) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const u64 o = (u64)convert<DT>(G::out(e));
+            e.step();
+            w[2 * q] = (u32)o;
+            w[2 * q + 1] = (u32)(o >> 32);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            w[q] = (u32)convert<DT>(G::out(e));
+            e.step();
+        }
+    }
+}
+
+// Same for the last, partial tile: only `cnt` more outputs are taken.
+template <typename G, int DT>
+__device__ __forceinline__ void gen16_partial(typename G::E &e, u32 (&w)[4], int cnt)
+{
+    typedef typename OutElem<DT>::type OT;
+    constexpr int PER = 16 / (int)sizeof(OT);
+    w[0] = w[1] = w[2] = w[3] = 0u;
+    for (int q = 0; q < PER && q < cnt; ++q) {
+        const u64 o = (u64)convert<DT>(G::out(e));
+        e.step();
+        if (sizeof(OT) == 8) {
+            w[2 * q] = (u32)o;
+            w[2 * q + 1] = (u32)(o >> 32);
+        } else {
+            w[q] = (u32)o;
+        }
+    }
+}
+
+// Generate one 32 x 128 B tile row for this lane into the swizzled tile:
+// 16-byte chunk c of row r lives at r * 128 + ((c ^ (r & 7)) * 16), so the 8
+// lanes of each quarter-warp hit 8 different bank groups.
+template <typename G, int DT>
+__device__ __forceinline__ void fill_tile_row(typename G::E &e, u32 tile, int lane, size_t left)
+{
+    typedef typename OutElem<DT>::type OT;
+    constexpr int COLS = 128 / (int)sizeof(OT);
+    constexpr int PER = 16 / (int)sizeof(OT);
+    const u32 row = tile + (u32)lane * 128u;
+    const u32 sw = (u32)(lane & 7);
+    if (left >= (size_t)COLS) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            u32 w[4];
+            gen16<G, DT>(e, w);
+            st_shared_v4(row + (((u32)c ^ sw) << 4), w[0], w[1], w[2], w[3]);
+        }
+    } else {
+        const int cnt = (int)left;
+        for (int c = 0; c < 8; ++c) {
+            u32 w[4];
+            gen16_partial<G, DT>(e, w, cnt - c * PER);
+            st_shared_v4(row + (((u32)c ^ sw) << 4), w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+template <int V, int DT>
+__global__ void __launch_bounds__(FILL_WARPS * 32)
+    k_fill_tma(const __grid_constant__ CUtensorMap map, void *states, size_t S, size_t m,
+               int write_back, int *status)
+{
+    typedef Gen<V> G;
+    typedef typename G::E E;
+    constexpr int COLS = 128 / (int)sizeof(typename OutElem<DT>::type);
+    extern __shared__ unsigned char dyn_smem[];
+    const u32 base = (smem_addr(dyn_smem) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t row0 = ((size_t)blockIdx.x * FILL_WARPS + warp) * 32;
+    if (row0 >= S) return;
+    const size_t i = row0 + lane;
+    const bool live = i < S;
+    E e;
+    if (live) {
+        load_state(e, (const char *)states + i * sizeof(e.s));
+        if (state_is_zero(e)) atomicCAS(status, 0, XR_EZERO_STATE);
+    } else {
+#pragma unroll
+        for (int j = 0; j < E::K; ++j) e.s[j] = 0;
+    }
+    const u32 tiles = base + (u32)(warp * FILL_NBUF * TILE_BYTES);
+    int it = 0;
+    for (size_t j0 = 0; j0 < m; j0 += COLS, ++it) {
+        const u32 tile = tiles + (u32)((it % FILL_NBUF) * TILE_BYTES);
+        if (it >= FILL_NBUF) {
+            if (lane == 0) bulk_wait_read<FILL_NBUF - 1>();
+            __syncwarp();
+        }
+        fill_tile_row<G, DT>(e, tile, lane, m - j0);
+        fence_proxy_async_shared();
+        __syncwarp();
+        if (lane == 0) {
+            tma_store_2d(&map, tile, (int)j0, (int)row0);
+            bulk_commit();
+        }
+    }
+    if (lane == 0) bulk_wait_all<0>();
+    if (write_back && live) store_state(e, (char *)states + i * sizeof(e.s));
+}
+
+__device__ __forceinline__ u64 ld_shared_u64(u32 a)
+{
+    u64 v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ u32 ld_shared_u32(u32 a)
+{
+    u32 v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
+// Same staging, then the warp writes its tile with element stores: any pitch,
+// any element-aligned pointer.
+template <int V, int DT>
+__global__ void __launch_bounds__(FILL_WARPS * 32)
+    k_fill_plain(void *states, size_t S, size_t m, size_t ld,
+                 typename OutElem<DT>::type *__restrict__ out, int write_back, int *status)
+{
+    typedef Gen<V> G;
+    typedef typename G::E E;
+    typedef typename OutElem<DT>::type OT;
+    constexpr int ES = (int)sizeof(OT);
+    constexpr int COLS = 128 / ES;
+    extern __shared__ unsigned char dyn_smem[];
+    const u32 base = (smem_addr(dyn_smem) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t row0 = ((size_t)blockIdx.x * FILL_WARPS + warp) * 32;
+    if (row0 >= S) return;
+    const size_t i = row0 + lane;
+    const bool live = i < S;
+    E e;
+    if (live) {
+        load_state(e, (const char *)states + i * sizeof(e.s));
+        if (state_is_zero(e)) atomicCAS(status, 0, XR_EZERO_STATE);
+    } else {
+#pragma unroll
+        for (int j = 0; j < E::K; ++j) e.s[j] = 0;
+    }
+    const u32 tile = base + (u32)(warp * FILL_NBUF * TILE_BYTES);
+    for (size_t j0 = 0; j0 < m; j0 += COLS) {
+        fill_tile_row<G, DT>(e, tile, lane, m - j0);
+        __syncwarp();
+        const int cols = (int)((m - j0) < (size_t)COLS ? (m - j0) : (size_t)COLS);
+        for (int f = lane; f < 32 * COLS; f += 32) {
+            const int r = f / COLS, c = f % COLS;
+            if (c >= cols || row0 + r >= S) continue;
+            const u32 byte = (u32)(c * ES);
+            const u32 a = tile + (u32)r * 128u + ((((byte >> 4) ^ (u32)(r & 7))) << 4) + (byte & 15u);
+            OT v;
+            if (ES == 8) v = (OT)ld_shared_u64(a);
+            else v = (OT)ld_shared_u32(a);
+            out[(row0 + r) * ld + j0 + c] = v;
+        }
+        __syncwarp();
+    }
+    if (write_back && live) store_state(e, (char *)states + i * sizeof(e.s));
+}
+
+// Interleaved layout: output j of all streams is contiguous, so the 32 lanes
+// of a warp store 32 consecutive elements per output.
+template <int V, int DT>
+__global__ void __launch_bounds__(256)
+    k_fill_interleaved(void *states, size_t S, size_t m,
+                       typename OutElem<DT>::type *__restrict__ out, int write_back, int *status)
+{
+    typedef Gen<V> G;
+    typedef typename G::E E;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    E e;
+    load_state(e, (const char *)states + i * sizeof(e.s));
+    if (state_is_zero(e)) atomicCAS(status, 0, XR_EZERO_STATE);
+#pragma unroll 4
+    for (size_t j = 0; j < m; ++j) {
+        out[j * S + i] = convert<DT>(G::out(e));
+        e.step();
+    }
+    if (write_back) store_state(e, (char *)states + i * sizeof(e.s));
+}
+
+template <int V, int DT>
+cudaError_t launch_fill_vd(int layout, void *states, size_t S, size_t m, size_t ld, void *out,
+                           int write_back, int *status, cudaStream_t stream, EncodeTiledFn encode)
+{
+    typedef typename OutElem<DT>::type OT;
+    constexpr int ES = (int)sizeof(OT);
+    constexpr int COLS = 128 / ES;
+    if (S == 0) return cudaSuccess;
+    if (layout == XR_INTERLEAVED) {
+        const size_t grid = (S + 255) / 256;
+        k_fill_interleaved<V, DT><<<(unsigned)grid, 256, 0, stream>>>(states, S, m, (OT *)out,
+                                                                     write_back, status);
+        count_launch();
+        return cudaGetLastError();
+    }
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e1 = cudaFuncSetAttribute(k_fill_tma<V, DT>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, FILL_SMEM);
+        cudaError_t e2 = cudaFuncSetAttribute(k_fill_plain<V, DT>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, FILL_SMEM);
+        if (e1 != cudaSuccess) return e1;
+        if (e2 != cudaSuccess) return e2;
+        attr_done = true;
+    }
+    const size_t rows_per_cta = (size_t)FILL_WARPS * 32;
+    const size_t grid = (S + rows_per_cta - 1) / rows_per_cta;
+    const bool tma_ok = encode != nullptr && ((uintptr_t)out % 16) == 0 && ((ld * ES) % 16) == 0 &&
+                        m < (1ull << 31) && S < (1ull << 31) && ld * ES < (1ull << 40) && m > 0;
+    if (tma_ok) {
+        CUtensorMap map;
+        const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)S};
+        const cuuint64_t strides[1] = {(cuuint64_t)(ld * ES)};
+        const cuuint32_t box[2] = {(cuuint32_t)COLS, 32u};
+        const cuuint32_t estr[2] = {1u, 1u};
+        const CUresult r = encode(&map, ES == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+                                  2, out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS) {
+            k_fill_tma<V, DT><<<(unsigned)grid, FILL_WARPS * 32, FILL_SMEM, stream>>>(
+                map, states, S, m, write_back, status);
+            count_launch();
+            return cudaGetLastError();
+        }
+    }
+    k_fill_plain<V, DT><<<(unsigned)grid, FILL_WARPS * 32, FILL_SMEM, stream>>>(
+        states, S, m, ld, (OT *)out, write_back, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Entry per generator: dtype dispatch over the element types it supports.
+template <int V>
+cudaError_t launch_fill_v(int dtype, int layout, void *states, size_t S, size_t m, size_t ld,
+                          void *out, int write_back, int *status, cudaStream_t stream,
+                          EncodeTiledFn encode)
+{
+    constexpr bool w64 = sizeof(typename Gen<V>::word) == 8;
+    switch (dtype) {
+    case DT_U64:
+        if constexpr (w64)
+            return launch_fill_vd<V, DT_U64>(layout, states, S, m, ld, out, write_back, status, stream, encode);
+        return cudaErrorInvalidValue;
+    case DT_U32:
+        if constexpr (!w64)
+            return launch_fill_vd<V, DT_U32>(layout, states, S, m, ld, out, write_back, status, stream, encode);
+        return cudaErrorInvalidValue;
+    case DT_F64:
+        return launch_fill_vd<V, DT_F64>(layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case DT_F32:
+        return launch_fill_vd<V, DT_F32>(layout, states, S, m, ld, out, write_back, status, stream, encode);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace xr

@@ -1,0 +1,53 @@
+// xr_internal.h -- host-side declarations shared by the libxr translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "xr.h"
+
+namespace xr {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Count one kernel launch (host-side, process-wide).
+void count_launch();
+
+// Engine of each variant and its state size in bits.
+int engine_of(int variant);
+int engine_bits(int engine);
+
+// Fill S streams x m outputs, row pitch ld elements (stream-major) or S
+// (interleaved).  `encode` may be NULL (plain-store path only).
+cudaError_t launch_fill(int variant, int dtype, int layout, void *states, size_t S, size_t m,
+                        size_t ld, void *out, int write_back, int *status, cudaStream_t stream,
+                        EncodeTiledFn encode);
+
+// Jump tables: tables holds n matrices T^(2^k), k = 0..n-1, each n columns of
+// n/32 words.  Built on `stream`.
+cudaError_t launch_build_tables(int engine, uint32_t *tables, cudaStream_t stream);
+
+// states[i] <- (prod over t of T^(2^ks[t])) states[i], i < count.
+struct KList {
+    int n;
+    int k[64];
+};
+cudaError_t launch_apply_pow(int engine, const uint32_t *tables, const KList &ks, void *states,
+                             size_t count, cudaStream_t stream);
+
+// Doubling tree: given states[0], fill states[1 .. S-1] with
+// states[i] = (T^(2^kbase))^i states[0] using T^(2^(kbase + L)) at level L.
+cudaError_t launch_tree(int engine, const uint32_t *tables, int kbase, void *states, size_t S,
+                        cudaStream_t stream);
+
+// SplitMix64 seeding: count states from d_seeds (or from `seed` when d_seeds
+// is NULL and count == 1).
+cudaError_t launch_seed(int variant, const uint64_t *d_seeds, uint64_t seed, size_t count,
+                        void *states, int *status, cudaStream_t stream);
+
+}  // namespace xr

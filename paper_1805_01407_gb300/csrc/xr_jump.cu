@@ -1,0 +1,280 @@
+// xr_jump.cu -- jump tables, jump-ahead and seeding kernels of libxr.
+//
+// Every engine is F2-linear (Sec. 3): one step is s' = T s for an n x n matrix
+// T over F2, so advancing e steps is T^e s.  The context keeps the powers
+// T^(2^k), k = 0 .. n-1 (T^(2^n) = T because the characteristic polynomial
+// is primitive, Sec. 6, so exponents wrap modulo n in k).  A jump by e * 2^d
+// steps multiplies by T^(2^(d+b)) for each set bit b of e; start states of
+// consecutive streams come from a doubling tree, one matrix-vector product per
+// stream: x_{2^L + i} = T^(2^(d+L)) x_i.
+#include "xr_device.cuh"
+#include "xr_internal.h"
+
+namespace xr {
+
+// ---------------------------------------------------------------- table build
+
+// Column c of T is the step of the unit state e_c (bit c set).
+template <int ENG>
+__global__ void k_build_T(u32 *T)
+{
+    typedef typename EngineOf<ENG>::type E;
+    constexpr int n = E::NBITS, NW = n / 32;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    u32 w[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) w[j] = (j == c / 32) ? (1u << (c % 32)) : 0u;
+    E e;
+    from_words(e, w);
+    e.step();
+    to_words(e, w);
+#pragma unroll
+    for (int j = 0; j < NW; ++j) T[(size_t)c * NW + j] = w[j];
+}
+
+// T^(2^(k+1)) = T^(2^k) T^(2^k): column c of the square is T^(2^k) applied to
+// column c of T^(2^k).  One CTA of n threads walks k = 0 .. n-2, keeping the
+// current matrix in shared memory (ping-pong) and writing every power out.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_square_chain(u32 *tables)
+{
+    constexpr int n = NW * 32;
+    __shared__ __align__(16) u32 M[2][n * NW];
+    const int c = threadIdx.x;
+    for (int t = c; t < n * NW; t += n) M[0][t] = tables[t];
+    __syncthreads();
+    for (int k = 0; k + 1 < n; ++k) {
+        const u32 *cur = M[k & 1];
+        u32 v[NW], r[NW];
+#pragma unroll
+        for (int j = 0; j < NW; ++j) v[j] = cur[c * NW + j];
+        f2_matvec<NW, true>(cur, v, r);
+        u32 *dst = tables + (size_t)(k + 1) * n * NW + (size_t)c * NW;
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+            dst[j] = r[j];
+            M[(k + 1) & 1][c * NW + j] = r[j];
+        }
+        __syncthreads();
+    }
+}
+
+template <int ENG>
+static cudaError_t build_tables_e(uint32_t *tables, cudaStream_t stream)
+{
+    typedef typename EngineOf<ENG>::type E;
+    constexpr int n = E::NBITS, NW = n / 32;
+    k_build_T<ENG><<<(n + 127) / 128, 128, 0, stream>>>(tables);
+    count_launch();
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    k_square_chain<NW><<<1, n, 0, stream>>>(tables);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_tables(int engine, uint32_t *tables, cudaStream_t stream)
+{
+    switch (engine) {
+    case ENG_XOSHIRO256: return build_tables_e<ENG_XOSHIRO256>(tables, stream);
+    case ENG_XOROSHIRO128: return build_tables_e<ENG_XOROSHIRO128>(tables, stream);
+    case ENG_XOROSHIRO128PP: return build_tables_e<ENG_XOROSHIRO128PP>(tables, stream);
+    case ENG_XOSHIRO128: return build_tables_e<ENG_XOSHIRO128>(tables, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------- apply powers
+
+template <int NW>
+__device__ __forceinline__ void load_vec(u32 (&v)[NW], const u32 *p)
+{
+#pragma unroll
+    for (int q = 0; q < NW / 4; ++q) {
+        const uint4 a = reinterpret_cast<const uint4 *>(p)[q];
+        v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void store_vec(const u32 (&v)[NW], u32 *p)
+{
+#pragma unroll
+    for (int q = 0; q < NW / 4; ++q)
+        reinterpret_cast<uint4 *>(p)[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+template <int NW>
+__global__ void __launch_bounds__(128)
+    k_apply_pow(const u32 *__restrict__ tables, KList ks, u32 *states, size_t count)
+{
+    constexpr int n = NW * 32;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    u32 v[NW], r[NW];
+    load_vec<NW>(v, states + i * NW);
+    for (int t = 0; t < ks.n; ++t) {
+        const u32 *M = tables + (size_t)ks.k[t] * n * NW;
+        f2_matvec<NW, false>(M, v, r);
+#pragma unroll
+        for (int j = 0; j < NW; ++j) v[j] = r[j];
+    }
+    store_vec<NW>(v, states + i * NW);
+}
+
+cudaError_t launch_apply_pow(int engine, const uint32_t *tables, const KList &ks, void *states,
+                             size_t count, cudaStream_t stream)
+{
+    if (count == 0 || ks.n == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((count + 127) / 128);
+    if (engine_bits(engine) == 256)
+        k_apply_pow<8><<<grid, 128, 0, stream>>>(tables, ks, (u32 *)states, count);
+    else
+        k_apply_pow<4><<<grid, 128, 0, stream>>>(tables, ks, (u32 *)states, count);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- doubling tree
+
+// Levels L while 2^L < min(S, 2 * blockDim): one CTA, the level matrix staged
+// in shared memory, a barrier between levels.
+template <int NW>
+__global__ void __launch_bounds__(256)
+    k_tree_small(const u32 *__restrict__ tables, int kbase, u32 *states, size_t S, int levels)
+{
+    constexpr int n = NW * 32;
+    __shared__ __align__(16) u32 M[n * NW];
+    for (int L = 0; L < levels; ++L) {
+        const u32 *src = tables + (size_t)((kbase + L) % n) * n * NW;
+        for (int t = threadIdx.x; t < n * NW / 4; t += blockDim.x)
+            reinterpret_cast<uint4 *>(M)[t] = reinterpret_cast<const uint4 *>(src)[t];
+        __syncthreads();
+        const size_t half = (size_t)1 << L;
+        const size_t idx = threadIdx.x;
+        if (idx < half && half + idx < S) {
+            u32 v[NW], r[NW];
+            load_vec<NW>(v, states + idx * NW);
+            f2_matvec<NW, true>(M, v, r);
+            store_vec<NW>(r, states + (half + idx) * NW);
+        }
+        __syncthreads();
+    }
+}
+
+// One level: states[half + idx] = M states[idx] for idx < min(half, S - half).
+template <int NW>
+__global__ void __launch_bounds__(256)
+    k_tree_level(const u32 *__restrict__ Mg, u32 *states, size_t half, size_t S)
+{
+    constexpr int n = NW * 32;
+    __shared__ __align__(16) u32 M[n * NW];
+    for (int t = threadIdx.x; t < n * NW / 4; t += blockDim.x)
+        reinterpret_cast<uint4 *>(M)[t] = reinterpret_cast<const uint4 *>(Mg)[t];
+    __syncthreads();
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= half || half + idx >= S) return;
+    u32 v[NW], r[NW];
+    load_vec<NW>(v, states + idx * NW);
+    f2_matvec<NW, true>(M, v, r);
+    store_vec<NW>(r, states + (half + idx) * NW);
+}
+
+template <int NW>
+static cudaError_t tree_nw(const uint32_t *tables, int kbase, void *states, size_t S,
+                           cudaStream_t stream)
+{
+    constexpr int n = NW * 32;
+    if (S <= 1) return cudaSuccess;
+    int small = 0;
+    while (small < 9 && ((size_t)1 << small) < S) ++small;  // 2^L <= 256 threads
+    k_tree_small<NW><<<1, 256, 0, stream>>>(tables, kbase, (u32 *)states, S, small);
+    count_launch();
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    for (int L = small; ((size_t)1 << L) < S; ++L) {
+        const size_t half = (size_t)1 << L;
+        const size_t work = (S - half) < half ? (S - half) : half;
+        const unsigned grid = (unsigned)((work + 255) / 256);
+        const uint32_t *M = tables + (size_t)((kbase + L) % n) * n * NW;
+        k_tree_level<NW><<<grid, 256, 0, stream>>>(M, (u32 *)states, half, S);
+        count_launch();
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_tree(int engine, const uint32_t *tables, int kbase, void *states, size_t S,
+                        cudaStream_t stream)
+{
+    if (engine_bits(engine) == 256) return tree_nw<8>(tables, kbase, states, S, stream);
+    return tree_nw<4>(tables, kbase, states, S, stream);
+}
+
+// ---------------------------------------------------------------- seeding
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014; Sec. 5.3): Weyl sequence with
+// increment 0x9e3779b97f4a7c15, then the 64-bit mixer (shifts 30, 27, 31;
+// multipliers 0xbf58476d1ce4e5b9, 0x94d049bb133111eb).
+__device__ __forceinline__ u64 splitmix64_next(u64 &x)
+{
+    x += 0x9e3779b97f4a7c15ull;
+    u64 z = x;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// WORDBYTES = 8: state word j = output j.  WORDBYTES = 4: output t gives words
+// 2t (low half) and 2t + 1 (high half).
+template <int WORDBYTES, int K>
+__global__ void k_seed(const u64 *__restrict__ seeds, u64 seed1, size_t count, u32 *states,
+                       int *status)
+{
+    constexpr int NW = WORDBYTES * K / 4;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    u64 x = seeds ? seeds[i] : seed1;
+    u32 w[NW];
+    if (WORDBYTES == 8) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const u64 z = splitmix64_next(x);
+            w[2 * j] = (u32)z;
+            w[2 * j + 1] = (u32)(z >> 32);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < K; j += 2) {
+            const u64 z = splitmix64_next(x);
+            w[j] = (u32)z;
+            w[j + 1] = (u32)(z >> 32);
+        }
+    }
+    u32 any = 0;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) any |= w[j];
+    if (!any) atomicCAS(status, 0, XR_EZERO_STATE);
+    store_vec<NW>(w, states + i * NW);
+}
+
+cudaError_t launch_seed(int variant, const uint64_t *d_seeds, uint64_t seed, size_t count,
+                        void *states, int *status, cudaStream_t stream)
+{
+    if (count == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((count + 127) / 128);
+    const int eng = engine_of(variant);
+    const u64 *sp = (const u64 *)d_seeds;
+    if (eng == ENG_XOSHIRO256)
+        k_seed<8, 4><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status);
+    else if (eng == ENG_XOSHIRO128)
+        k_seed<4, 4><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status);
+    else
+        k_seed<8, 2><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace xr

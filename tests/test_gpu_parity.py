@@ -1,0 +1,365 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every integer result is compared bit for bit; doubles and floats are compared
+as bit patterns too (the conversions are exact, Sec. 5.3, so the tolerance is
+zero).  Small shapes cover single values, partial tiles and ragged tails;
+the full-size configurations are checked on sampled streams.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from xr_testutil import (assert_bits_equal, dense_from_library_columns, dense_from_oracle_rows,
+                         expected, out_to_numpy, states_from_device, states_to_bytes,
+                         states_to_device)
+
+pytestmark = pytest.mark.gpu
+
+GUARD = 64          # canary elements on each side of an output buffer
+CANARY = 0x5A
+
+
+@pytest.fixture(scope="module")
+def xr():
+    from paper_1805_01407_gb300 import build
+    build.build()
+    import paper_1805_01407_gb300 as xr
+    return xr
+
+
+@pytest.fixture(scope="module")
+def ctx(xr):
+    import torch
+    assert torch.cuda.is_available()
+    c = xr.Context(0)
+    yield c
+    c.close()
+
+
+def guarded_output(xr, n, dtype, offset=0):
+    """Output view of n elements with canary bytes on both sides."""
+    import torch
+    es = xr.dtype_bytes(dtype)
+    total = (n + 2 * GUARD) * es + offset
+    raw = torch.full((total,), CANARY, dtype=torch.uint8, device="cuda")
+    start = GUARD * es + offset
+    view = raw[start:start + n * es]
+    return raw, view, start, n * es
+
+
+def check_canaries(raw, start, nbytes):
+    r = raw.cpu().numpy()
+    assert (r[:start] == CANARY).all(), "write before the output"
+    assert (r[start + nbytes:] == CANARY).all(), "write past the output"
+
+
+def as_dtype(view, dtype):
+    import torch
+    tdt = {"u64": torch.int64, "u32": torch.int32, "f64": torch.float64, "f32": torch.float32}[dtype]
+    return view.view(tdt)
+
+
+# ------------------------------------------------------------------ tables
+
+@pytest.mark.parametrize("name", ["xoshiro256**", "xoroshiro128+", "xoroshiro128++", "xoshiro128++"])
+def test_jump_tables_match_oracle(ctx, xr, name):
+    """T built on the device by stepping unit states equals the oracle's T (which
+    equals the paper's block matrix); the squaring chain gives T^2, T^(2^d) and
+    wraps around (T^(2^n) = T)."""
+    n = O.state_bits(name)
+    T = O.matrix_from_step(name)
+    assert (dense_from_library_columns(ctx.jump_table(name, 0), n) == dense_from_oracle_rows(T)).all()
+    T2 = O.mat_mul(T, T)
+    assert (dense_from_library_columns(ctx.jump_table(name, 1), n) == dense_from_oracle_rows(T2)).all()
+    d = xr.jump_log2(name, "jump")
+    Td = O.mat_pow2(T, d)
+    assert (dense_from_library_columns(ctx.jump_table(name, d), n) == dense_from_oracle_rows(Td)).all()
+    last = dense_from_library_columns(ctx.jump_table(name, n - 1), n)
+    sq = (last.astype(np.int64) @ last.astype(np.int64)) % 2
+    assert (sq == dense_from_oracle_rows(T)).all()
+
+
+# ------------------------------------------------------------------ seeding
+
+@pytest.mark.parametrize("name", W.ALL_VARIANTS)
+def test_seed(ctx, xr, name):
+    import torch
+    for seed in (0, 1, 42, 0x0123456789ABCDEF, 2**64 - 1):
+        st = ctx.empty_states(name, 1)
+        ctx.seed(name, seed, st)
+        torch.cuda.synchronize()
+        assert (states_from_device(name, st)[0] == O.seed(name, seed)).all()
+        assert ctx.get_state(name, st) == states_to_bytes(name, O.seed(name, seed))
+
+
+def test_seed_many(ctx, xr):
+    import torch
+    seeds = torch.arange(4096, dtype=torch.int64, device="cuda")
+    for name in ("xoshiro256++", "xoroshiro128**", "xoshiro128**"):
+        st = ctx.empty_states(name, 4096)
+        ctx.seed_many(name, seeds, st)
+        got = states_from_device(name, st)
+        for s in (0, 1, 17, 4095):
+            assert (got[s] == O.seed(name, s)).all()
+        want = np.stack([O.seed(name, s) for s in range(4096)])
+        assert (got == want).all()
+
+
+# ------------------------------------------------------------------ fill
+
+@pytest.mark.parametrize("name", W.ALL_VARIANTS)
+@pytest.mark.parametrize("layout", ["stream", "interleaved"])
+def test_fill_small_shapes(ctx, xr, name, layout):
+    """All dtypes and shapes with ragged tails, canaries, write-back."""
+    import torch
+    w = O.word_bits(name)
+    for si, (S, m) in enumerate(W.PARITY_SHAPES):
+        starts = W.random_states(O.state_words(name), w, S, seed=1000 + si)
+        raw = O.fill_streams(name, starts, m).reshape(S, m)
+        for dtype in (xr.native_dtype(name), "f64", "f32"):
+            d_states = states_to_device(name, starts)
+            buf, view, start, nb = guarded_output(xr, S * m, dtype)
+            ctx.fill(name, d_states, S, m, dtype, as_dtype(view, dtype), layout=layout, write_back=True)
+            torch.cuda.synchronize()
+            check_canaries(buf, start, nb)
+            got = out_to_numpy(as_dtype(view, dtype), dtype).reshape((S, m) if layout == "stream" else (m, S))
+            if layout == "interleaved":
+                got = got.T
+            want = expected(name, raw.reshape(-1), dtype).reshape(S, m)
+            assert_bits_equal(got.reshape(-1), want.reshape(-1), "%s %s S=%d m=%d" % (name, dtype, S, m))
+            after = states_from_device(name, d_states)
+            for i in (0, S // 2, S - 1):
+                assert (after[i] == O.step(name, starts[i], m)).all()
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("name", ["xoshiro256**", "xoroshiro128++", "xoshiro128**"])
+def test_fill_unaligned_output_and_no_write_back(ctx, xr, name):
+    """An output pointer that is element- but not 16-byte aligned takes the
+    plain-store path; without write-back the states are unchanged."""
+    import torch
+    S, m = 77, 40
+    starts = W.random_states(O.state_words(name), O.word_bits(name), S, seed=7)
+    raw = O.fill_streams(name, starts, m)
+    for dtype in (xr.native_dtype(name), "f64"):
+        es = xr.dtype_bytes(dtype)
+        d_states = states_to_device(name, starts)
+        buf, view, start, nb = guarded_output(xr, S * m, dtype, offset=es)
+        ctx.fill(name, d_states, S, m, dtype, as_dtype(view, dtype))
+        torch.cuda.synchronize()
+        check_canaries(buf, start, nb)
+        assert_bits_equal(out_to_numpy(as_dtype(view, dtype), dtype), expected(name, raw, dtype))
+        assert (states_from_device(name, d_states) == starts).all()
+
+
+def test_fill_continues_across_calls(ctx, xr):
+    """Write-back makes two fills of m outputs equal one fill of 2m."""
+    import torch
+    name = "xoshiro256++"
+    S, m = 500, 48
+    starts = W.random_states(4, 64, S, seed=9)
+    d_states = states_to_device(name, starts)
+    a = ctx.empty_output(S * m, "u64")
+    b = ctx.empty_output(S * m, "u64")
+    ctx.fill(name, d_states, S, m, "u64", a, write_back=True)
+    ctx.fill(name, d_states, S, m, "u64", b, write_back=True)
+    torch.cuda.synchronize()
+    raw = O.fill_streams(name, starts, 2 * m).reshape(S, 2 * m)
+    assert_bits_equal(out_to_numpy(a, "u64").reshape(S, m), raw[:, :m])
+    assert_bits_equal(out_to_numpy(b, "u64").reshape(S, m), raw[:, m:])
+
+
+# ------------------------------------------------------------------ jumps
+
+@pytest.mark.parametrize("name", ["xoshiro256++", "xoroshiro128**", "xoroshiro128++", "xoshiro128++"])
+def test_jump_and_advance(ctx, xr, name):
+    import torch
+    k, w = O.state_words(name), O.word_bits(name)
+    states = W.random_states(k, w, 100, seed=11)
+    for kind in ("jump", "long"):
+        d = O.jump_log2(name, kind)
+        for times in (1, 2, 5, 2**33 + 1):
+            t = states_to_device(name, states)
+            ctx.jump(name, kind, t, 100, times)
+            got = states_from_device(name, t)
+            for i in (0, 1, 50, 99):
+                assert (got[i] == O.jump_pow(name, d, times, states[i])).all(), (kind, times, i)
+    for nsteps in (1, 3, 1000, 2**40 + 12345):
+        t = states_to_device(name, states)
+        ctx.advance(name, t, 100, nsteps)
+        got = states_from_device(name, t)
+        for i in (0, 42, 99):
+            want = O.step(name, states[i], nsteps) if nsteps <= 1000 else O.jump_pow(name, 0, nsteps, states[i])
+            assert (got[i] == want).all(), (nsteps, i)
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("name", ["xoshiro256++", "xoroshiro128**", "xoroshiro128++", "xoshiro128**"])
+@pytest.mark.parametrize("kind", ["jump", "long"])
+def test_make_streams(ctx, xr, name, kind):
+    """Stream i = J^(first + i)(base), against one jump after another."""
+    base = O.seed(name, 42)
+    d_base = states_to_device(name, base[None, :])
+    for S, first in ((1, 0), (2, 0), (3, 5), (257, 0), (1000, 1), (3000, 777), (600, 2**40 + 5)):
+        out = ctx.empty_states(name, S)
+        ctx.make_streams(name, kind, d_base, first, S, out)
+        got = states_from_device(name, out)
+        want = O.streams(name, kind, base, S, first=first)
+        assert (got == want).all(), (S, first)
+
+
+def test_make_streams_rejects_overlap(ctx, xr):
+    name = "xoshiro256**"
+    t = ctx.empty_states(name, 10)
+    ctx.seed(name, 1, t)
+    with pytest.raises(xr.XRError):
+        ctx.make_streams(name, "jump", t, 0, 10, t)
+
+
+# ------------------------------------------------------------------ one long sequence
+
+@pytest.mark.parametrize("name", ["xoshiro256**", "xoroshiro128+", "xoroshiro128++", "xoshiro128++"])
+def test_fill_seq(ctx, xr, name):
+    import torch
+    s0 = O.seed(name, 123)
+    for n in (1, 2, 17, 1023, 1024, 1025, 4096, 70001):
+        raw, after = O.generate(name, s0, n)
+        for dtype in (xr.native_dtype(name), "f64"):
+            d_state = states_to_device(name, s0[None, :])
+            buf, view, start, nb = guarded_output(xr, n, dtype)
+            ctx.fill_seq(name, d_state, n, dtype, as_dtype(view, dtype))
+            torch.cuda.synchronize()
+            check_canaries(buf, start, nb)
+            assert_bits_equal(out_to_numpy(as_dtype(view, dtype), dtype), expected(name, raw, dtype),
+                              "%s n=%d" % (name, n))
+            assert (states_from_device(name, d_state)[0] == after).all()
+
+
+# ------------------------------------------------------------------ configurations
+
+def test_plain_configuration_full(ctx, xr):
+    """xoshiro256**, SplitMix64(0x0123456789ABCDEF), 1024 streams made by 1023
+    successive jumps, 1024 outputs each: every value, as uint64 and double."""
+    import torch
+    c = W.CONFIG_PLAIN
+    name, S, m = c["variant"], c["S"], c["m"]
+    base = O.seed(name, c["seed"])
+    starts = O.streams(name, "jump", base, S)          # one jump after another
+    raw = O.fill_streams(name, starts, m)
+    d_base = ctx.empty_states(name, 1)
+    ctx.seed(name, c["seed"], d_base)
+    d_states = ctx.empty_states(name, S)
+    ctx.make_streams(name, "jump", d_base, 0, S, d_states)
+    assert (states_from_device(name, d_states) == starts).all()
+    for dtype in c["dtypes"]:
+        out = ctx.empty_output(S * m, dtype)
+        ctx.fill(name, d_states, S, m, dtype, out)
+        torch.cuda.synchronize()
+        assert_bits_equal(out_to_numpy(out, dtype), expected(name, raw, dtype), dtype)
+        if dtype == "f64":
+            v = out_to_numpy(out, dtype)
+            assert v.min() >= 0.0 and v.max() < 1.0
+            assert_bits_equal(v, (raw >> np.uint64(11)).astype(np.float64) * 2.0**-53)
+
+
+@pytest.mark.parametrize("name", W.BULK_VARIANTS)
+def test_bulk_configuration_sampled(ctx, xr, name):
+    """2^20 streams x 2^10 outputs from SplitMix64(42) in the launch
+    configuration the benchmark times; 66 sampled streams compared in full."""
+    import torch
+    c = W.CONFIG_BULK
+    S, m = c["S"], c["m"]
+    base = O.seed(name, c["seed"])
+    d = O.jump_log2(name, c["kind"])
+    idx = W.sample_indices(S, 66, seed=3)
+    d_base = ctx.empty_states(name, 1)
+    ctx.seed(name, c["seed"], d_base)
+    d_states = ctx.empty_states(name, S)
+    ctx.make_streams(name, c["kind"], d_base, 0, S, d_states)
+    got_states = states_from_device(name, d_states)
+    for dtype in (xr.native_dtype(name), "f64"):
+        out = ctx.empty_output(S * m, dtype)
+        ctx.fill(name, d_states, S, m, dtype, out)
+        torch.cuda.synchronize()
+        rows = out.view(S, m)[torch.as_tensor(idx, device="cuda")]
+        got = out_to_numpy(rows.contiguous(), dtype).reshape(len(idx), m)
+        for r, i in enumerate(idx):
+            st = O.jump_pow(name, d, int(i), base)
+            assert (got_states[i] == st).all()
+            raw, _ = O.generate(name, st, m)
+            assert_bits_equal(got[r], expected(name, raw, dtype), "%s %s stream %d" % (name, dtype, i))
+        del out
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("kind", ["jump", "long"])
+def test_jumpstart_configuration_sampled(ctx, xr, kind):
+    """2^24 xoshiro256++ streams J^i(s0) / L^i(s0), 64 outputs each: 4096
+    sampled streams against the oracle's jump power, and the first 2048 start
+    states against one CPU jump after another."""
+    import torch
+    c = W.CONFIG_JUMPSTART
+    name, S, m = c["variant"], c["S"], c["m"]
+    base = O.seed(name, c["seed"])
+    d = O.jump_log2(name, kind)
+    d_base = ctx.empty_states(name, 1)
+    ctx.seed(name, c["seed"], d_base)
+    d_states = ctx.empty_states(name, S)
+    ctx.make_streams(name, kind, d_base, 0, S, d_states)
+    out = ctx.empty_output(S * m, "u64")
+    ctx.fill(name, d_states, S, m, "u64", out)
+    torch.cuda.synchronize()
+    got_states = states_from_device(name, d_states)
+    assert (got_states[:2048] == O.streams(name, kind, base, 2048)).all()
+    idx = W.sample_indices(S, c["samples"], c["sample_seed"])
+    rows = out_to_numpy(out.view(S, m)[torch.as_tensor(idx, device="cuda")].contiguous(), "u64")
+    rows = rows.reshape(len(idx), m)
+    for r, i in enumerate(idx):
+        st = O.jump_pow(name, d, int(i), base)
+        assert (got_states[i] == st).all(), int(i)
+        raw, _ = O.generate(name, st, m)
+        assert_bits_equal(rows[r], raw, "stream %d" % i)
+
+
+def test_fill_host_chunks(ctx, xr):
+    """End-to-end call into host memory, large enough for three staging chunks."""
+    import torch
+    name = "xoshiro256**"
+    S, m = (1 << 16) + 100, 1 << 10
+    base = O.seed(name, 5)
+    h_out = torch.empty(S * m, dtype=torch.int64).pin_memory()
+    ctx.fill_host(name, "jump", states_to_bytes(name, base), 7, S, m, "u64", h_out)
+    got = h_out.numpy().view(np.uint64).reshape(S, m)
+    d = O.jump_log2(name, "jump")
+    for i in W.sample_indices(S, 24, seed=5):
+        raw, _ = O.generate(name, O.jump_pow(name, d, 7 + int(i), base), m)
+        assert_bits_equal(got[i], raw, "stream %d" % i)
+
+
+# ------------------------------------------------------------------ errors
+
+def test_zero_state_is_reported(ctx, xr):
+    import torch
+    name = "xoroshiro128+"
+    t = ctx.empty_states(name, 4)
+    with pytest.raises(xr.XRError) as e:
+        ctx.set_state(name, bytes(16), t)
+    assert e.value.status == xr.XR_EZERO_STATE
+    assert ctx.status(reset=True) == 0
+    out = ctx.empty_output(4 * 8, "u64")
+    ctx.fill(name, t, 4, 8, "u64", out)                # all four states are zero
+    torch.cuda.synchronize()
+    assert ctx.status() == xr.XR_EZERO_STATE
+    assert ctx.status(reset=True) == xr.XR_EZERO_STATE
+    assert ctx.status() == 0
+
+
+def test_invalid_arguments(ctx, xr):
+    t = ctx.empty_states("xoshiro256**", 1)
+    out = ctx.empty_output(16, "u64")
+    with pytest.raises(xr.XRError) as e:
+        ctx.fill("xoshiro256**", t, 1, 16, "u32", out)
+    assert e.value.status == xr.XR_EINVAL
+    with pytest.raises(ValueError):
+        ctx.fill("xoshiro256**", t, 1, 17, "u64", out)   # buffer too small

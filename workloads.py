@@ -1,0 +1,65 @@
+"""Seeded synthetic workloads: shapes, seeds and sampled indices only.
+
+This module holds none of the generators' arithmetic.  Both the CUDA-path
+tests/bench and the oracle-side checks take their inputs from here, so the two
+sides see identical problems.  The paper's workloads are the generators'
+own output streams (no dataset is involved); the configurations below fix
+the seeds, stream counts, lengths and mixes used for parity and timing.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Generators of the bulk-fill configuration (64-bit: +, ++, ** on xoshiro256
+# and xoroshiro128; 32-bit: ++ and ** on xoshiro128).
+BULK_VARIANTS = (
+    "xoshiro256+", "xoshiro256++", "xoshiro256**",
+    "xoroshiro128+", "xoroshiro128++", "xoroshiro128**",
+    "xoshiro128**", "xoshiro128++",
+)
+ALL_VARIANTS = BULK_VARIANTS + ("xoshiro128+",)
+
+# xoshiro256**, SplitMix64(0x0123456789ABCDEF), 1024 streams by successive
+# jumps, 1024 outputs each, as raw uint64 and as doubles.
+CONFIG_PLAIN = dict(variant="xoshiro256**", seed=0x0123456789ABCDEF, kind="jump", S=1024, m=1024,
+                    dtypes=("u64", "f64"))
+
+# Bulk fill: every generator, SplitMix64(42) base, 2^20 streams by jumps,
+# 2^10 outputs each (2^30 values), native words and doubles.
+CONFIG_BULK = dict(variants=BULK_VARIANTS, seed=42, kind="jump", S=1 << 20, m=1 << 10)
+
+# Jump-start at scale: 2^24 xoshiro256++ streams J^i(s0) and L^i(s0), 64
+# outputs each; 4096 uniformly sampled stream indices (seed 1) are checked.
+CONFIG_JUMPSTART = dict(variant="xoshiro256++", seed=42, kinds=("jump", "long"), S=1 << 24, m=64,
+                        samples=4096, sample_seed=1)
+
+
+def native_dtype(variant: str) -> str:
+    return "u32" if variant.startswith("xoshiro128") else "u64"
+
+
+def sample_indices(S: int, count: int, seed: int) -> np.ndarray:
+    """Sorted distinct stream indices in [0, S): 0 and S-1 plus uniform draws."""
+    rng = np.random.default_rng(seed)
+    if count >= S:
+        return np.arange(S, dtype=np.int64)
+    idx = set([0, S - 1])
+    while len(idx) < count:
+        idx.update(int(x) for x in rng.integers(0, S, size=count))
+    return np.array(sorted(idx)[:count], dtype=np.int64)
+
+
+# (S, m) shapes for element-by-element parity: single values, partial tiles,
+# several 32-stream tiles and 128-byte rows, ragged tails in both dimensions.
+PARITY_SHAPES = ((1, 1), (1, 15), (2, 17), (31, 16), (33, 33), (129, 100), (300, 64),
+                 (257, 1000), (1000, 48))
+
+
+def random_states(k: int, w: int, count: int, seed: int) -> np.ndarray:
+    """count nonzero states of k words of w bits (uint64 array [count, k])."""
+    rng = np.random.default_rng(seed)
+    hi = np.uint64(2**w - 1) if w < 64 else np.uint64(2**64 - 1)
+    out = rng.integers(0, hi, size=(count, k), dtype=np.uint64, endpoint=True)
+    zero = ~out.any(axis=1)
+    out[zero, 0] = 1
+    return out
