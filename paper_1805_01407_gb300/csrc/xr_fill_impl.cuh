@@ -245,8 +245,12 @@ cudaError_t launch_fill_vd(int layout, void *states, size_t S, size_t m, size_t 
     }
     const size_t rows_per_cta = (size_t)FILL_WARPS * 32;
     const size_t grid = (S + rows_per_cta - 1) / rows_per_cta;
+    // The tile store clips columns past the extent only to a 16-byte boundary
+    // (seen on GB300: a 4-byte row received 16 bytes), so the row length must
+    // be a multiple of 16 bytes as well as the pitch.
     const bool tma_ok = encode != nullptr && ((uintptr_t)out % 16) == 0 && ((ld * ES) % 16) == 0 &&
-                        m < (1ull << 31) && S < (1ull << 31) && ld * ES < (1ull << 40) && m > 0;
+                        ((m * ES) % 16) == 0 && m < (1ull << 31) && S < (1ull << 31) &&
+                        ld * ES < (1ull << 40) && m > 0;
     if (tma_ok) {
         CUtensorMap map;
         const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)S};
