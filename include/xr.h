@@ -171,6 +171,30 @@ int xr_fill(xr_ctx *ctx, int variant, void *d_states, size_t S, size_t m, int dt
 int xr_fill_seq(xr_ctx *ctx, int variant, void *d_state, size_t n, int dtype, void *d_out,
                 void *stream);
 
+/* xr_fill_seq_noalloc: xr_fill_seq for callers that cannot allocate device
+ * memory during the call -- for example code that runs while the application
+ * owns all device memory through its own pool, or inside a real-time or
+ * callback path where cudaMalloc/cudaFree would block, synchronize the device
+ * or fail.  (The paper has no counterpart: this is a property of the
+ * library, not of the method.)  The outputs and the advanced state are the
+ * ones xr_fill_seq gives.
+ *   - Allocates nothing: the segment start states live in one static device
+ *     array of XR_NOALLOC_MAX_OUTPUTS / 1024 states x 32 bytes (2 MiB) that
+ *     every GPU loading the library holds until the process exits.  The
+ *     context (created earlier) supplies the jump tables.
+ *   - n > XR_NOALLOC_MAX_OUTPUTS returns XR_EINVAL and enqueues nothing.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current, cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   - All calls in the process share the array, which keeps the last call's
+ *     contents; nothing in it needs to start at zero, since every slot a call
+ *     reads is written earlier in the same call.  Calls that overlap on the
+ *     GPU (different streams, or different threads without ordering) race on
+ *     the array and give wrong outputs: serialize them. */
+#define XR_NOALLOC_MAX_OUTPUTS ((size_t)1 << 26)
+int xr_fill_seq_noalloc(xr_ctx *ctx, int variant, void *d_state, size_t n, int dtype, void *d_out,
+                        void *stream);
+
 /* xr_fill_host: end-to-end call with host memory.  Copies one base state from
  * h_base (host), makes S streams J^(first + i)(base), generates S x m outputs
  * (stream-major) and copies them to h_out (host, S * m elements of dtype;

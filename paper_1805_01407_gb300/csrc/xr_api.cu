@@ -58,6 +58,8 @@ using namespace xr;
 
 // Segment length of xr_fill_seq: 2^SEQ_LOG2 outputs per segment.
 static const int SEQ_LOG2 = 10;
+// Segment length of xr_fill_seq_noalloc (same as xr_fill_seq).
+#define SEQ_LOG2_NOALLOC 10
 // Largest staging buffer of xr_fill_host (two of them).
 static const size_t HOST_STAGING_BYTES = (size_t)256 << 20;
 
@@ -472,5 +474,61 @@ extern "C" int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_ba
     cudaError_t e3 = cudaStreamSynchronize(st);
     if (err == cudaSuccess) err = e2;
     if (err == cudaSuccess) err = e3;
+    return status_of(err);
+}
+
+// ---------------------------------------------------------------- no-allocation variant
+//
+// xr_fill_seq_noalloc: the same computation as xr_fill_seq, for callers that
+// must not allocate device memory while they run (see include/xr.h).  The
+// segment start states live in the file-scope device array below instead of
+// context scratch, so the call itself never calls cudaMalloc or cudaFree.
+
+static __device__ __align__(256) unsigned char g_noalloc_segments[XR_NOALLOC_MAX_OUTPUTS >> SEQ_LOG2_NOALLOC][32];
+
+// Device address of g_noalloc_segments on each device, looked up once per
+// device (with that device current) by the first call made on it.  In host
+// code the array's name is only a host-side stand-in, never a device address.
+static std::atomic<void *> g_noalloc_addr[64];
+
+static int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return XR_ECUDA;
+    void *p = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        if (cudaGetSymbolAddress(&p, g_noalloc_segments) != cudaSuccess || !p) return XR_ECUDA;
+        g_noalloc_addr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return XR_OK;
+}
+
+extern "C" int xr_fill_seq_noalloc(xr_ctx *ctx, int variant, void *d_state, size_t n, int dtype,
+                                   void *d_out, void *stream)
+{
+    if (!ctx || !variant_ok(variant) || !dtype_ok(variant, dtype)) return XR_EINVAL;
+    if (n > (size_t)XR_NOALLOC_MAX_OUTPUTS) return XR_EINVAL;
+    if (n == 0) return XR_OK;
+    const size_t es = (size_t)xr_dtype_bytes(dtype);
+    if (!states_ok(d_state) || !d_out || ((uintptr_t)d_out % es)) return XR_EINVAL;
+    void *scratch = NULL;
+    const int rc = noalloc_scratch(&scratch);
+    if (rc != XR_OK) return rc;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const size_t seg = (size_t)1 << SEQ_LOG2_NOALLOC;
+    const size_t full = n / seg, tail = n % seg, P = full + (tail ? 1 : 0);
+    const size_t sb = (size_t)xr_state_bytes(variant);
+    // Every slot read below is written first in this call (the base copy and
+    // the doubling tree fill slots 0 .. P-1), so nothing has to start at zero.
+    cudaError_t err = make_streams(ctx, variant, SEQ_LOG2_NOALLOC, d_state, 0, P, scratch, st);
+    if (err == cudaSuccess && full)
+        err = launch_fill(variant, dtype, XR_STREAM_MAJOR, scratch, full, seg, seg, d_out, 1,
+                          ctx->d_status, st, ctx->encode);
+    if (err == cudaSuccess && tail)
+        err = launch_fill(variant, dtype, XR_STREAM_MAJOR, (char *)scratch + full * sb, 1, tail, seg,
+                          (char *)d_out + full * seg * es, 1, ctx->d_status, st, ctx->encode);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(d_state, (char *)scratch + (P - 1) * sb, sb, cudaMemcpyDeviceToDevice, st);
     return status_of(err);
 }
