@@ -63,9 +63,13 @@ static const int SEQ_LOG2 = 10;
 // Largest staging buffer of xr_fill_host (two of them).
 static const size_t HOST_STAGING_BYTES = (size_t)256 << 20;
 
+// Jump distances with power sets, per engine: jump, long jump, xr_fill_seq segment.
+static const int NUM_PSET_DISTS = 3;
+
 struct xr_ctx {
     int device;
     uint32_t *tables[NUM_ENGINES];
+    uint32_t *psets[NUM_ENGINES];  // NUM_PSET_DISTS x PSET_LEVELS power sets
     int *d_status;
     void *scratch;            // segment start states of xr_fill_seq
     size_t scratch_bytes;
@@ -167,12 +171,24 @@ static bool dtype_ok(int variant, int dtype)
 
 // ---------------------------------------------------------------- context
 
+// Jump distances (log2) that get power sets: jump, long jump, fill_seq segment.
+static void pset_dists(int engine, int *d)
+{
+    const int n = engine_bits(engine);
+    d[0] = n / 2;
+    d[1] = 3 * n / 4;
+    d[2] = 10;
+}
+
 extern "C" int xr_ctx_destroy(xr_ctx *ctx)
 {
     if (!ctx) return XR_OK;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    for (int e = 0; e < NUM_ENGINES; ++e) cudaFree(ctx->tables[e]);
+    for (int e = 0; e < NUM_ENGINES; ++e) {
+        cudaFree(ctx->tables[e]);
+        cudaFree(ctx->psets[e]);
+    }
     cudaFree(ctx->d_status);
     cudaFree(ctx->scratch);
     for (int b = 0; b < 2; ++b) {
@@ -207,6 +223,12 @@ extern "C" int xr_ctx_create(int device, xr_ctx **out)
         const size_t n = (size_t)engine_bits(e);
         rc = status_of(cudaMalloc((void **)&ctx->tables[e], n * n * n / 8));
         if (rc == XR_OK) rc = status_of(launch_build_tables(e, ctx->tables[e], 0));
+        const size_t pset_bytes = (size_t)NUM_PSET_DISTS * PSET_LEVELS * PSET_SIZE * n * n / 8;
+        if (rc == XR_OK) rc = status_of(cudaMalloc((void **)&ctx->psets[e], pset_bytes));
+        int dists[NUM_PSET_DISTS];
+        pset_dists(e, dists);
+        if (rc == XR_OK)
+            rc = status_of(launch_build_power_sets(e, ctx->tables[e], dists, NUM_PSET_DISTS, ctx->psets[e], 0));
     }
     if (rc == XR_OK) rc = status_of(cudaMalloc((void **)&ctx->d_status, sizeof(int)));
     if (rc == XR_OK) rc = status_of(cudaMemset(ctx->d_status, 0, sizeof(int)));
@@ -333,6 +355,14 @@ static cudaError_t make_streams(xr_ctx *ctx, int variant, int d, const void *d_b
         err = launch_apply_pow(e, ctx->tables[e], klist(first, d, engine_bits(e)), out, 1, st);
         if (err != cudaSuccess) return err;
     }
+    int dists[NUM_PSET_DISTS];
+    pset_dists(e, dists);
+    const size_t n = (size_t)engine_bits(e);
+    for (int di = 0; di < NUM_PSET_DISTS; ++di)
+        if (dists[di] == d && S <= ((size_t)1 << (PSET_BITS * PSET_LEVELS))) {
+            const size_t set_words = (size_t)PSET_SIZE * n * (n / 32);
+            return launch_streams_psets(e, ctx->psets[e] + (size_t)di * PSET_LEVELS * set_words, out, S, st);
+        }
     return launch_tree(e, ctx->tables[e], d, out, S, st);
 }
 

@@ -157,18 +157,37 @@ __device__ __forceinline__ bool state_is_zero(const E &e)
 // Output element codes (match xr_dtype).
 enum { DT_U64 = 0, DT_U32 = 1, DT_F64 = 2, DT_F32 = 3 };
 
-// (x >> 11) * 2^-53 as binary64 bits, built with integer operations only.  With
-// v = x >> 11 != 0 and lz = clz64(v) (11 <= lz <= 63), the leading one of v is
-// bit p = 63 - lz, the value is 1.f * 2^(p - 53), so the biased exponent is
-// p + 970 and the fraction is v << (52 - p) without its leading one.  Adding
-// the shifted v (whose leading one lands on bit 52) to (p + 969) << 52 sets both
-// at once: bits = (v << (lz - 11)) + ((1032 - lz) << 52).  v = 0 gives +0.0.
+// (x >> 11) * 2^-53 as binary64 bits, built with integer operations only.
+//
+// Rare path, x < 2^32: v = x >> 11 < 2^21; with its leading one at bit p the
+// value is 1.f * 2^(p - 53): biased exponent p + 970, fraction v << (52 - p)
+// without the leading one; v = 0 gives +0.0.
+static __device__ __noinline__ u64 unit_f64_bits_small(u64 x)
+{
+    const u32 v = (u32)(x >> 11);
+    if (v == 0u) return 0ull;
+    const int p = 31 - __clz(v);
+    const u64 frac = ((u64)v << (52 - p)) & ((1ull << 52) - 1);
+    return ((u64)(p + 970) << 52) | frac;
+}
+
+// Common path, high word hi != 0 with lz = clz(hi) <= 31.  Clearing the 11 low
+// bits of x and shifting left by lz puts the leading one of x >> 11 at bit 63;
+// bits 63..11 of that are the 53-bit significand, leading one at bit 52.  The
+// value is 1.f * 2^(-1 - lz): biased exponent 1022 - lz; since the leading one
+// (bit 20 of the high word) already adds one to the exponent field, adding
+// (1021 - lz) << 20 to the high word completes the encoding.
 __device__ __forceinline__ u64 unit_f64_bits(u64 x)
 {
-    const u64 v = x >> 11;
-    const int lz = __clzll(v);
-    const u64 bits = (v << (lz - 11)) + ((u64)(1032 - lz) << 52);
-    return v ? bits : 0ull;
+    const u32 hi = (u32)(x >> 32);
+    if (__builtin_expect(hi == 0u, 0)) return unit_f64_bits_small(x);
+    const u32 lo = (u32)x & 0xFFFFF800u;
+    const int lz = __clz(hi);
+    const u32 yh = __funnelshift_l(lo, hi, lz);
+    const u32 yl = lo << lz;
+    const u32 mh = (yh >> 11) + ((u32)(1021 - lz) << 20);
+    const u32 ml = __funnelshift_r(yl, yh, 11);
+    return ((u64)mh << 32) | ml;
 }
 
 // x * 2^-32 as binary64 bits for a 32-bit word: leading one at bit p = 31 - lz,

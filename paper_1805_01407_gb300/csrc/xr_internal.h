@@ -45,6 +45,19 @@ cudaError_t launch_apply_pow(int engine, const uint32_t *tables, const KList &ks
 cudaError_t launch_tree(int engine, const uint32_t *tables, int kbase, void *states, size_t S,
                         cudaStream_t stream);
 
+// Power sets for three-level stream starts: per engine, for each jump distance
+// 2^d in `dists` and level l < PSET_LEVELS, PSET_SIZE matrices P_l[j] =
+// (T^(2^(d + PSET_BITS l)))^j, stored set after set (distance-major).
+constexpr int PSET_BITS = 9;
+constexpr int PSET_SIZE = 1 << PSET_BITS;
+constexpr int PSET_LEVELS = 3;
+cudaError_t launch_build_power_sets(int engine, const uint32_t *tables, const int *dists, int ndist,
+                                    uint32_t *sets, cudaStream_t stream);
+// Given states[0], fill states[1 .. S-1] (S <= 2^(PSET_BITS * PSET_LEVELS))
+// with states[i] = (T^(2^d))^i states[0], sets3 = the three sets of distance d.
+cudaError_t launch_streams_psets(int engine, const uint32_t *sets3, void *states, size_t S,
+                                 cudaStream_t stream);
+
 // SplitMix64 seeding: count states from d_seeds (or from `seed` when d_seeds
 // is NULL and count == 1).
 cudaError_t launch_seed(int variant, const uint64_t *d_seeds, uint64_t seed, size_t count,

@@ -213,6 +213,120 @@ cudaError_t launch_tree(int engine, const uint32_t *tables, int kbase, void *sta
     return tree_nw<4>(tables, kbase, states, S, stream);
 }
 
+// ---------------------------------------------------------------- power sets
+//
+// Stream starts in three levels instead of a tree of depth log2(S).  For a
+// jump distance 2^d and level l = 0, 1, 2 the context keeps the power set
+//   P_l[j] = (T^(2^(d + 9 l)))^j,   j = 0 .. 511,
+// built once by doubling: P_l[0] = I and, for j in [2^L, 2^(L+1)),
+// P_l[j] = T^(2^(d + 9 l + L)) P_l[j - 2^L], the multiplier being a jump-table
+// entry.  Writing the stream index in base 512, i = p * 512^(l+1) + j * 512^l,
+// stream i is P_l[j] applied to stream p * 512^(l+1), which an earlier (higher)
+// level wrote; so the states array itself holds every intermediate level and
+// each level is one launch reading only entries it does not write.
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_pset_identity(u32 *sets)
+{
+    constexpr int n = NW * 32;
+    const int c = threadIdx.x;
+    u32 *col = sets + (size_t)blockIdx.x * PSET_SIZE * n * NW + (size_t)c * NW;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) col[w] = (w == c / 32) ? (1u << (c % 32)) : 0u;
+}
+
+// Level L of the doubling: P[j] = T^(2^k) P[j - 2^L], j = 2^L + blockIdx.x,
+// set blockIdx.y, column threadIdx.x; k = (kfirst[set] + L) mod n.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32)
+    k_pset_level(const u32 *__restrict__ tables, u32 *sets, KList kfirst, int L)
+{
+    constexpr int n = NW * 32;
+    __shared__ __align__(16) u32 M[n * NW];
+    const int set = blockIdx.y, c = threadIdx.x;
+    const int j = (1 << L) + blockIdx.x;
+    const u32 *src = tables + (size_t)((kfirst.k[set] + L) % n) * n * NW;
+    for (int t = c; t < n * NW / 4; t += n)
+        reinterpret_cast<uint4 *>(M)[t] = reinterpret_cast<const uint4 *>(src)[t];
+    __syncthreads();
+    u32 *P = sets + (size_t)set * PSET_SIZE * n * NW;
+    u32 v[NW], r[NW];
+    load_vec<NW>(v, P + (size_t)(j - (1 << L)) * n * NW + (size_t)c * NW);
+    f2_matvec<NW, true>(M, v, r);
+    store_vec<NW>(r, P + (size_t)j * n * NW + (size_t)c * NW);
+}
+
+cudaError_t launch_build_power_sets(int engine, const uint32_t *tables, const int *dists, int ndist,
+                                    uint32_t *sets, cudaStream_t stream)
+{
+    const int n = engine_bits(engine);
+    KList kf;
+    kf.n = ndist * PSET_LEVELS;
+    for (int di = 0; di < ndist; ++di)
+        for (int l = 0; l < PSET_LEVELS; ++l) kf.k[di * PSET_LEVELS + l] = (dists[di] + PSET_BITS * l) % n;
+    const int nsets = kf.n;
+    if (n == 256) k_pset_identity<8><<<nsets, 256, 0, stream>>>((u32 *)sets);
+    else k_pset_identity<4><<<nsets, 128, 0, stream>>>((u32 *)sets);
+    count_launch();
+    cudaError_t err = cudaGetLastError();
+    for (int L = 0; L < PSET_BITS && err == cudaSuccess; ++L) {
+        const dim3 grid(1u << L, (unsigned)nsets);
+        if (n == 256) k_pset_level<8><<<grid, 256, 0, stream>>>(tables, (u32 *)sets, kf, L);
+        else k_pset_level<4><<<grid, 128, 0, stream>>>(tables, (u32 *)sets, kf, L);
+        count_launch();
+        err = cudaGetLastError();
+    }
+    return err;
+}
+
+// One level: for every parent p (index p * 512 * stride) and j in 1 .. 511,
+// states[p * 512 * stride + j * stride] = P[j] states[p * 512 * stride].  The
+// CTA shares j (blockIdx.y + 1) and stages P[j] in shared memory.
+template <int NW>
+__global__ void __launch_bounds__(256)
+    k_streams_level(const u32 *__restrict__ P, u32 *states, size_t S, size_t stride, size_t nparents)
+{
+    constexpr int n = NW * 32;
+    __shared__ __align__(16) u32 M[n * NW];
+    const int j = blockIdx.y + 1;
+    const u32 *src = P + (size_t)j * n * NW;
+    for (int t = threadIdx.x; t < n * NW / 4; t += blockDim.x)
+        reinterpret_cast<uint4 *>(M)[t] = reinterpret_cast<const uint4 *>(src)[t];
+    __syncthreads();
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nparents) return;
+    const size_t parent = p * PSET_SIZE * stride;
+    const size_t child = parent + (size_t)j * stride;
+    if (child >= S) return;
+    u32 v[NW], r[NW];
+    load_vec<NW>(v, states + parent * NW);
+    f2_matvec<NW, true>(M, v, r);
+    store_vec<NW>(r, states + child * NW);
+}
+
+cudaError_t launch_streams_psets(int engine, const uint32_t *sets3, void *states, size_t S,
+                                 cudaStream_t stream)
+{
+    const int n = engine_bits(engine);
+    if (S <= 1) return cudaSuccess;
+    const size_t set_words = (size_t)PSET_SIZE * n * (n / 32);
+    int top = 0;
+    while (top + 1 < PSET_LEVELS && S > ((size_t)1 << (PSET_BITS * (top + 1)))) ++top;
+    for (int l = top; l >= 0; --l) {
+        const size_t stride = (size_t)1 << (PSET_BITS * l);
+        const size_t span = stride * PSET_SIZE;
+        const size_t nparents = (S + span - 1) / span;
+        const dim3 grid((unsigned)((nparents + 255) / 256), PSET_SIZE - 1);
+        const uint32_t *P = sets3 + (size_t)l * set_words;
+        if (n == 256) k_streams_level<8><<<grid, 256, 0, stream>>>(P, (u32 *)states, S, stride, nparents);
+        else k_streams_level<4><<<grid, 256, 0, stream>>>(P, (u32 *)states, S, stride, nparents);
+        count_launch();
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
 // ---------------------------------------------------------------- seeding
 
 // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014; Sec. 5.3): Weyl sequence with

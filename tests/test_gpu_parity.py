@@ -170,6 +170,33 @@ def test_fill_continues_across_calls(ctx, xr):
     assert_bits_equal(out_to_numpy(b, "u64").reshape(S, m), raw[:, m:])
 
 
+@pytest.mark.parametrize("name,w", [("xoshiro256+", 64), ("xoroshiro128+", 64), ("xoshiro128+", 32)])
+def test_conversion_edge_values(ctx, xr, name, w):
+    """Crafted + states whose first output is an edge value of the double and
+    float conversions (0, values below 2^11, around 2^32, the top of the range):
+    the + output is s_p + s_q, so (x, ..., 0) emits x first."""
+    import torch
+    k = O.state_words(name)
+    X = [0, 1, 2**11 - 1, 2**11, 2**12 + 5, 2**24 - 1, 2**31, 2**32 - 1]
+    if w == 64:
+        X += [2**32, 2**32 + 2**31, 2**43 + 1, 2**53, 2**63, 2**64 - 1, 2**64 - 2**11]
+    starts = []
+    for x in X:
+        if k == 2:          # xoroshiro128+: s0 + s1
+            starts.append([x, 0] if x else [2**63, 2**63])
+        else:               # xoshiro: s0 + s3
+            starts.append([x, 0x1234567, 0x89ABCDE, 0])
+    starts = np.array(starts, dtype=np.uint64)
+    raw = O.fill_streams(name, starts, 16)
+    assert [int(v) for v in raw.reshape(len(X), 16)[:, 0]] == X
+    for dtype in ("f64", "f32", xr.native_dtype(name)):
+        d_states = states_to_device(name, starts)
+        out = ctx.empty_output(len(X) * 16, dtype)
+        ctx.fill(name, d_states, len(X), 16, dtype, out)
+        torch.cuda.synchronize()
+        assert_bits_equal(out_to_numpy(out, dtype), expected(name, raw, dtype), dtype)
+
+
 # ------------------------------------------------------------------ jumps
 
 @pytest.mark.parametrize("name", ["xoshiro256++", "xoroshiro128**", "xoroshiro128++", "xoshiro128++"])
@@ -201,12 +228,30 @@ def test_make_streams(ctx, xr, name, kind):
     """Stream i = J^(first + i)(base), against one jump after another."""
     base = O.seed(name, 42)
     d_base = states_to_device(name, base[None, :])
-    for S, first in ((1, 0), (2, 0), (3, 5), (257, 0), (1000, 1), (3000, 777), (600, 2**40 + 5)):
+    for S, first in ((1, 0), (2, 0), (3, 5), (257, 0), (512, 0), (513, 3), (1000, 1), (3000, 777),
+                     (600, 2**40 + 5)):
         out = ctx.empty_states(name, S)
         ctx.make_streams(name, kind, d_base, first, S, out)
         got = states_from_device(name, out)
         want = O.streams(name, kind, base, S, first=first)
         assert (got == want).all(), (S, first)
+
+
+@pytest.mark.parametrize("name", ["xoshiro256**", "xoroshiro128++"])
+def test_make_streams_three_levels_sampled(ctx, xr, name):
+    """More than 2^18 streams use all three levels of the start-state scheme;
+    sampled indices around every level boundary against the oracle."""
+    base = O.seed(name, 99)
+    d_base = states_to_device(name, base[None, :])
+    S, first = (1 << 18) + 1000, 12345
+    out = ctx.empty_states(name, S)
+    ctx.make_streams(name, "jump", d_base, first, S, out)
+    got = states_from_device(name, out)
+    d = O.jump_log2(name, "jump")
+    idx = sorted(set([0, 1, 511, 512, 513, 1023, 1024, 262143, 262144, 262145, S - 1]) |
+                 set(int(i) for i in W.sample_indices(S, 40, seed=4)))
+    for i in idx:
+        assert (got[i] == O.jump_pow(name, d, first + i, base)).all(), i
 
 
 def test_make_streams_rejects_overlap(ctx, xr):
