@@ -47,6 +47,8 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batched-steps", type=int, default=5)
     p.add_argument("--profile", choices=["fill", "streams"], default=None,
                    help="run a small case for an ncu capture instead of the benchmark")
     p.add_argument("--profile-variant", default="xoshiro256**")
@@ -362,6 +364,8 @@ def run_xr(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if not args.no_batched:
+        line["batched"] = run_batched(xr, ctx, args)
     if not args.no_e2e:
         line["e2e"] = run_e2e(ctx, args, first, bytes_per_step, world, dist)
     if dist:
@@ -371,6 +375,69 @@ def run_xr(args):
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0
+
+
+def run_batched(xr, ctx, args):
+    """Batched uneven requests: 4096 requests (lengths log-uniform in [1, 2^24],
+    8 generators, native/double, SplitMix64(r) seeds) in one persistent launch
+    captured in a CUDA graph and tuned, against the plain path of one xr_seed +
+    xr_fill_seq per request, on the same GPU and output arena."""
+    import torch
+    specs = W.batch_requests(**W.CONFIG_BATCH)
+    seeds = [s for (_, _, _, s) in specs]
+    reqs, offs, arena = xr.pack_requests([(v, dt, n, r) for r, (v, dt, n, _) in enumerate(specs)])
+    nbytes = sum(n * dtype_bytes(dt) for (_, dt, n, _) in specs)
+    b = xr.Batch(ctx, reqs)
+    slots = torch.zeros(len(specs) * 32, dtype=torch.uint8, device="cuda")
+    out = torch.empty(arena, dtype=torch.uint8, device="cuda")
+    d_seeds = torch.tensor(seeds, dtype=torch.int64, device="cuda")
+    tune_ms = b.tune(d_seeds, slots, out)
+    opt, block = b.get_config()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        b.run(d_seeds, slots, out, use_graph=True)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.batched_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(d_seeds, slots, out, use_graph=True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    batch_ms = statistics.median(times)
+    # plain: one seed + one xr_fill_seq per request, events around each request
+    st = ctx.empty_states("xoshiro256**", 1)
+    views = {d: out.view(xr.torch_dtype(d)) for d in ("u64", "u32", "f64")}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in specs]
+    plain_ms = []
+    for rep in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for r, (v, dt, n, _) in enumerate(specs):
+            if rep:
+                ev[r][0].record(stream)
+            ctx.seed(v, seeds[r], st)
+            es = dtype_bytes(dt)
+            ctx.fill_seq(v, st, n, dt, views[dt][offs[r] // es: offs[r] // es + n])
+            if rep:
+                ev[r][1].record(stream)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+    per_req = sorted(ev[r][0].elapsed_time(ev[r][1]) for r in range(len(specs)))
+    b.close()
+    q = lambda p: per_req[min(len(per_req) - 1, int(p * len(per_req)))]
+    return {
+        "workload": "4096 requests, lengths log-uniform in [1, 2^24] (%.1f GB), 8 generators, "
+                    "native/f64, SplitMix64(r) seeds; one persistent launch in a CUDA graph" % (nbytes / 1e9),
+        "value": nbytes / (batch_ms / 1e3) / 1e9, "unit": UNIT, "ms": batch_ms,
+        "plain_value": nbytes / (plain_ms[-1] / 1e3) / 1e9, "plain_ms": plain_ms[-1],
+        "speedup_vs_plain": plain_ms[-1] / batch_ms,
+        "plain_request_ms_p50": q(0.5), "plain_request_ms_p99": q(0.99),
+        "tuned": {"outputs_per_row": opt, "block": block, "best_trial_ms": tune_ms},
+        "tasks": b.tasks if False else None,
+    }
 
 
 def run_e2e(ctx, args, first, bytes_per_step, world, dist):

@@ -204,6 +204,64 @@ int xr_fill_seq_noalloc(xr_ctx *ctx, int variant, void *d_state, size_t n, int d
 int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_base, uint64_t first,
                  size_t S, size_t m, int dtype, void *h_out, void *stream);
 
+/* ---- batching: many uneven requests in one persistent launch ---------------
+ * A request asks for the first n outputs of one sequence (as xr_fill_seq),
+ * starting from the state in slot `slot` of a caller-owned state table of
+ * 32-byte slots (16-byte states use the first half), and writes them at byte
+ * offset `out_offset` (a multiple of 16) of a caller-owned output arena.  When
+ * the batch runs, every request's slot is advanced by its n steps, so the
+ * next batch continues each sequence.  Two requests of one batch must not
+ * share a slot.  Optionally each slot is first seeded with SplitMix64 from a
+ * per-request seed (Sec. 5.3).
+ *
+ * The plan groups requests by (variant, dtype), cuts them into segments of
+ * 1024 outputs whose start states come from jump-ahead (power sets, three
+ * launches for the whole batch), and packs 32 segments per warp task.  One
+ * persistent kernel pulls tasks from a device queue; each lane writes its
+ * rows with its own bulk copies, so segments of different requests share a
+ * warp.  Results equal xr_fill_seq on each request alone, bit for bit. */
+typedef struct {
+    int variant;          /* xr_variant */
+    int dtype;            /* xr_dtype valid for the variant */
+    uint64_t n;           /* outputs (0 allowed: only seeding, if any) */
+    uint64_t slot;        /* state slot index */
+    uint64_t out_offset;  /* byte offset in the output arena, multiple of 16 */
+} xr_request;
+
+typedef struct xr_batch xr_batch;
+
+/* Plan a batch: checks the requests (XR_EINVAL on a bad variant/dtype, an
+ * unaligned offset or a slot used twice), copies the plan to device memory
+ * owned by the batch and sizes its scratch.  h_reqs is read during the call
+ * only.  The batch keeps using ctx (which must outlive it). */
+int xr_batch_create(xr_ctx *ctx, const xr_request *h_reqs, size_t nreq, xr_batch **out);
+int xr_batch_destroy(xr_batch *b);
+
+/* Bytes of output arena the batch writes (max of out_offset + n * element
+ * size over requests), and the number of warp tasks / segments. */
+uint64_t xr_batch_arena_bytes(const xr_batch *b);
+uint64_t xr_batch_tasks(const xr_batch *b);
+
+/* Run the batch on `stream`: d_seeds (device, one uint64 per request, or
+ * NULL to use the slots as they are), d_slots (device state table), d_out
+ * (device arena, 16-byte aligned).  With use_graph != 0 the launches are
+ * captured into a CUDA graph on the first run with these pointers and the
+ * graph is replayed on later runs (a different pointer set recaptures). */
+int xr_batch_run(xr_batch *b, const uint64_t *d_seeds, void *d_slots, void *d_out, int use_graph,
+                 void *stream);
+
+/* Launch configuration of the persistent kernel: outputs per staged row
+ * (4, 8, 16, 32 or 64) and threads per block (128, 256 or 512). */
+int xr_batch_set_config(xr_batch *b, int outputs_per_row, int block);
+int xr_batch_get_config(const xr_batch *b, int *outputs_per_row, int *block);
+
+/* Autotune: time every (outputs_per_row, block) pair that fits in shared
+ * memory on this batch (each trial restores d_slots first), keep the
+ * fastest, restore d_slots and report the best time in *best_ms.  Blocks
+ * on `stream`. */
+int xr_batch_tune(xr_batch *b, const uint64_t *d_seeds, void *d_slots, void *d_out, void *stream,
+                  float *best_ms);
+
 /* ---- status and inspection ------------------------------------------------ */
 
 /* Sticky device status: XR_OK, or the first error a kernel recorded

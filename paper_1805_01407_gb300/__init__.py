@@ -35,6 +35,12 @@ XR_OK, XR_EINVAL, XR_EZERO_STATE, XR_ENOMEM, XR_ECUDA, XR_ETIMEOUT, XR_EUNSUPPOR
 _lib = None
 
 
+class Request(ctypes.Structure):
+    """xr_request of include/xr.h."""
+    _fields_ = [("variant", ctypes.c_int), ("dtype", ctypes.c_int), ("n", ctypes.c_uint64),
+                ("slot", ctypes.c_uint64), ("out_offset", ctypes.c_uint64)]
+
+
 class XRError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -76,6 +82,22 @@ def lib():
         }
         L.xr_launch_count.argtypes = []
         L.xr_launch_count.restype = ctypes.c_uint64
+        L.xr_batch_create.argtypes = [vp, ctypes.POINTER(Request), sz, ctypes.POINTER(vp)]
+        L.xr_batch_create.restype = i
+        L.xr_batch_destroy.argtypes = [vp]
+        L.xr_batch_destroy.restype = i
+        L.xr_batch_arena_bytes.argtypes = [vp]
+        L.xr_batch_arena_bytes.restype = ctypes.c_uint64
+        L.xr_batch_tasks.argtypes = [vp]
+        L.xr_batch_tasks.restype = ctypes.c_uint64
+        L.xr_batch_run.argtypes = [vp, vp, vp, vp, i, vp]
+        L.xr_batch_run.restype = i
+        L.xr_batch_set_config.argtypes = [vp, i, i]
+        L.xr_batch_set_config.restype = i
+        L.xr_batch_get_config.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.xr_batch_get_config.restype = i
+        L.xr_batch_tune.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]
+        L.xr_batch_tune.restype = i
         for name, args in sigs.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -285,3 +307,78 @@ class Context:
         buf = ctypes.create_string_buffer(n * n // 8)
         _check(lib().xr_jump_table(self._h, _v(variant), k, buf), "xr_jump_table")
         return buf.raw
+
+
+def pack_requests(specs, align=256):
+    """Lay out requests in one output arena.
+
+    specs: iterable of (variant, dtype, n[, slot]); slot defaults to the
+    request's index.  Returns (list of Request, list of byte offsets, arena
+    bytes); every request starts on an `align`-byte boundary."""
+    reqs, offs, off = [], [], 0
+    for r, spec in enumerate(specs):
+        v, dt, n = spec[0], spec[1], int(spec[2])
+        slot = int(spec[3]) if len(spec) > 3 else r
+        reqs.append(Request(_v(v), DTYPES[dt], n, slot, off))
+        offs.append(off)
+        off += (n * dtype_bytes(dt) + align - 1) // align * align
+    return reqs, offs, off
+
+
+class Batch:
+    """Many uneven requests in one persistent launch (xr_batch_*)."""
+
+    def __init__(self, ctx, requests):
+        self.ctx = ctx
+        arr = (Request * len(requests))(*requests)
+        h = ctypes.c_void_p()
+        _check(lib().xr_batch_create(ctx.handle, arr, len(requests), ctypes.byref(h)), "xr_batch_create")
+        self._h = h
+        self.nreq = len(requests)
+        self.max_slot = max((r.slot for r in requests), default=0)
+
+    @property
+    def arena_bytes(self):
+        return lib().xr_batch_arena_bytes(self._h)
+
+    @property
+    def tasks(self):
+        return lib().xr_batch_tasks(self._h)
+
+    def _args(self, d_seeds, d_slots, d_out):
+        if d_seeds is not None:
+            _need(d_seeds, self.nreq * 8, "d_seeds")
+        _need(d_slots, (self.max_slot + 1) * 32, "d_slots")
+        if self.arena_bytes:
+            _need(d_out, self.arena_bytes, "d_out")
+        return (ctypes.c_void_p(d_seeds.data_ptr() if d_seeds is not None else None),
+                ctypes.c_void_p(d_slots.data_ptr()), ctypes.c_void_p(d_out.data_ptr() if d_out is not None else None))
+
+    def run(self, d_seeds, d_slots, d_out, use_graph=False, stream=None):
+        a = self._args(d_seeds, d_slots, d_out)
+        _check(lib().xr_batch_run(self._h, *a, int(bool(use_graph)), _stream(stream)), "xr_batch_run")
+
+    def tune(self, d_seeds, d_slots, d_out, stream=None):
+        a = self._args(d_seeds, d_slots, d_out)
+        ms = ctypes.c_float()
+        _check(lib().xr_batch_tune(self._h, *a, _stream(stream), ctypes.byref(ms)), "xr_batch_tune")
+        return ms.value
+
+    def set_config(self, outputs_per_row, block):
+        _check(lib().xr_batch_set_config(self._h, outputs_per_row, block), "xr_batch_set_config")
+
+    def get_config(self):
+        o, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().xr_batch_get_config(self._h, ctypes.byref(o), ctypes.byref(b)), "xr_batch_get_config")
+        return o.value, b.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().xr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -27,6 +27,7 @@ static const int kEngineOf[XR_NUM_VARIANTS] = {ENG_XOSHIRO256, ENG_XOSHIRO256, E
                                                ENG_XOROSHIRO128, ENG_XOROSHIRO128PP, ENG_XOROSHIRO128,
                                                ENG_XOSHIRO128, ENG_XOSHIRO128, ENG_XOSHIRO128};
 static const int kEngineBits[NUM_ENGINES] = {256, 128, 128, 128};
+static_assert(NUM_ENGINES == NUM_ENGINES_H, "engine count");
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -62,25 +63,6 @@ static const int SEQ_LOG2 = 10;
 #define SEQ_LOG2_NOALLOC 10
 // Largest staging buffer of xr_fill_host (two of them).
 static const size_t HOST_STAGING_BYTES = (size_t)256 << 20;
-
-// Jump distances with power sets, per engine: jump, long jump, xr_fill_seq segment.
-static const int NUM_PSET_DISTS = 3;
-
-struct xr_ctx {
-    int device;
-    uint32_t *tables[NUM_ENGINES];
-    uint32_t *psets[NUM_ENGINES];  // NUM_PSET_DISTS x PSET_LEVELS power sets
-    int *d_status;
-    void *scratch;            // segment start states of xr_fill_seq
-    size_t scratch_bytes;
-    void *staging[2];         // output staging of xr_fill_host
-    void *chunk_states[2];    // stream start states of xr_fill_host
-    void *base_state;         // one state (xr_fill_host)
-    size_t staging_bytes, chunk_states_bytes;
-    cudaStream_t side;        // copy stream of xr_fill_host
-    cudaEvent_t ev_gen[2], ev_copy[2];
-    EncodeTiledFn encode;
-};
 
 static const char *kNames[XR_NUM_VARIANTS] = {
     "xoshiro256+", "xoshiro256++", "xoshiro256**", "xoroshiro128+", "xoroshiro128++",
@@ -179,6 +161,24 @@ static void pset_dists(int engine, int *d)
     d[1] = 3 * n / 4;
     d[2] = 10;
 }
+
+namespace xr {
+int pset_index(int engine, int d)
+{
+    int dists[NUM_PSET_DISTS];
+    pset_dists(engine, dists);
+    for (int di = 0; di < NUM_PSET_DISTS; ++di)
+        if (dists[di] == d) return di;
+    return -1;
+}
+
+const uint32_t *pset_sets(const xr_ctx *ctx, int engine, int di)
+{
+    const size_t n = (size_t)engine_bits(engine);
+    const size_t set_words = (size_t)PSET_SIZE * n * (n / 32);
+    return ctx->psets[engine] + (size_t)di * PSET_LEVELS * set_words;
+}
+}  // namespace xr
 
 extern "C" int xr_ctx_destroy(xr_ctx *ctx)
 {

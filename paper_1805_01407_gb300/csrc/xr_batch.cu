@@ -1,0 +1,653 @@
+// xr_batch.cu -- many uneven generation requests in one persistent launch.
+//
+// A request is "the first n outputs of the sequence in state slot s" (the
+// semantics of xr_fill_seq).  The host plan cuts every request into segments
+// of 2^10 outputs.  Segment q of a request starts at T^(q 2^10) s, computed by
+// the three-level power-set scheme (xr_jump.cu), batched over requests.
+// Requests with the same (generator, dtype) form a group whose segments are
+// numbered consecutively; a warp task is 32 consecutive segments of a group,
+// so small requests share warps without divergent code paths.  One persistent
+// kernel pulls tasks from a device counter.  Each lane stages its rows in its
+// own shared-memory buffers and writes them with its own bulk copies
+// (cp.async.bulk), so lanes of different requests never wait for each other.
+#include <algorithm>
+#include <stdlib.h>
+#include <string.h>
+#include <vector>
+
+#include "xr_device.cuh"
+#include "xr_internal.h"
+
+namespace xr {
+
+constexpr int BSEG_LOG2 = 10;            // outputs per segment = 1024
+constexpr u64 BSEG = 1ull << BSEG_LOG2;
+constexpr int BATCH_NBUF = 2;            // staged rows per lane
+constexpr int SLOT_WORDS = 8;            // 32-byte state slots
+
+struct BReq {
+    u64 n, out_offset, slot, seg_base;
+    int variant, dtype;
+};
+
+struct BGroup {
+    int variant, dtype;
+    u32 nreq, req_first;
+    u64 nseg, prefix_first;
+};
+
+struct BLevelItem {
+    u64 parent, limit;  // parent segment index (absolute) and end of its request's segments
+};
+
+struct BatchDev {
+    const BReq *reqs;
+    const BGroup *groups;
+    const u32 *group_reqs;
+    const u64 *prefix;
+    const u64 *tasks;
+    u64 ntasks;
+    unsigned long long *counter;
+    u32 *segstates;
+    unsigned char *slots;
+    unsigned char *out;
+    const u64 *seeds;
+    int *status;
+    int opt;            // outputs per staged row
+    u32 bufstride;      // bytes between consecutive lanes' buffers
+};
+
+// ---------------------------------------------------------------- seeding / copy-in
+
+// Slot state (or SplitMix64 of the request's seed, also written to the slot)
+// becomes segment 0 of the request.
+__global__ void k_batch_seed(BatchDev d, size_t nreq)
+{
+    const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nreq) return;
+    const BReq q = d.reqs[r];
+    u32 w[SLOT_WORDS];
+    u32 *slot = reinterpret_cast<u32 *>(d.slots + q.slot * 32);
+    const int eng = (q.variant <= 2) ? 0 : (q.variant <= 5 ? 1 : 3);
+    if (d.seeds) {
+        u64 x = d.seeds[r];
+#pragma unroll
+        for (int j = 0; j < SLOT_WORDS; ++j) w[j] = 0u;
+        if (eng == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const u64 z = splitmix64_next(x);
+                w[2 * j] = (u32)z;
+                w[2 * j + 1] = (u32)(z >> 32);
+            }
+        } else {
+            // xoroshiro128: two 64-bit words; xoshiro128: each output gives two
+            // 32-bit words, low half first -- the same four u32 words either way.
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const u64 z = splitmix64_next(x);
+                w[2 * j] = (u32)z;
+                w[2 * j + 1] = (u32)(z >> 32);
+            }
+        }
+        reinterpret_cast<uint4 *>(slot)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<uint4 *>(slot)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    } else {
+        const uint4 a = reinterpret_cast<const uint4 *>(slot)[0];
+        const uint4 b = reinterpret_cast<const uint4 *>(slot)[1];
+        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+        w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+        if (eng != 0) w[4] = w[5] = w[6] = w[7] = 0u;
+    }
+    u32 any = 0;
+#pragma unroll
+    for (int j = 0; j < SLOT_WORDS; ++j) any |= w[j];
+    if (!any) atomicCAS(d.status, 0, XR_EZERO_STATE);
+    if (q.n > 0) {
+        uint4 *dst = reinterpret_cast<uint4 *>(d.segstates + q.seg_base * SLOT_WORDS);
+        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+// ---------------------------------------------------------------- segment starts
+
+// One level of the power-set scheme over many requests of one engine:
+// segstates[parent + j * stride] = P[j] segstates[parent] when inside the
+// request (below `limit`).  The CTA shares j and stages P[j] in shared memory.
+template <int NW>
+__global__ void __launch_bounds__(256)
+    k_batch_level(const u32 *__restrict__ P, const BLevelItem *__restrict__ items, size_t nitems,
+                  u64 stride, u32 *segstates)
+{
+    constexpr int n = NW * 32;
+    __shared__ __align__(16) u32 M[n * NW];
+    const int j = blockIdx.y + 1;
+    const u32 *src = P + (size_t)j * n * NW;
+    for (int t = threadIdx.x; t < n * NW / 4; t += blockDim.x)
+        reinterpret_cast<uint4 *>(M)[t] = reinterpret_cast<const uint4 *>(src)[t];
+    __syncthreads();
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nitems) return;
+    const BLevelItem it = items[idx];
+    const u64 child = it.parent + (u64)j * stride;
+    if (child >= it.limit) return;
+    u32 v[NW], r[NW];
+    const uint4 *ps = reinterpret_cast<const uint4 *>(segstates + it.parent * SLOT_WORDS);
+#pragma unroll
+    for (int q = 0; q < NW / 4; ++q) {
+        const uint4 a = ps[q];
+        v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+    }
+    f2_matvec<NW, true>(M, v, r);
+    uint4 *cs = reinterpret_cast<uint4 *>(segstates + child * SLOT_WORDS);
+#pragma unroll
+    for (int q = 0; q < NW / 4; ++q) cs[q] = make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    if (NW == 4) cs[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// ---------------------------------------------------------------- persistent fill
+
+__device__ __forceinline__ void bulk_store_s2g(void *gdst, u32 ssrc, u32 bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ u64 lds_u64(u32 a)
+{
+    u64 v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ u32 lds_u32(u32 a)
+{
+    u32 v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
+// One lane, one segment: `count` outputs from the state at `st`, written at
+// `out`; rows of opt outputs are staged in two shared buffers and written by
+// bulk copies (a trailing piece under 16 bytes by plain stores).  With
+// `slot` non-null the final state is stored there.
+template <int V, int DT>
+__device__ __forceinline__ void batch_lane(const u32 *st, unsigned char *slot, unsigned char *out,
+                                           u64 count, u32 buf0, u32 bufnext, int opt)
+{
+    typedef Gen<V> G;
+    typedef typename G::E E;
+    typedef typename OutElem<DT>::type OT;
+    constexpr int ES = (int)sizeof(OT), PER = 16 / ES;
+    E e;
+    load_state(e, st);
+    const int chunks = opt * ES / 16;
+    int it = 0;
+    for (u64 j0 = 0; j0 < count; j0 += (u64)opt, ++it) {
+        const u32 buf = buf0 + (u32)(it & 1) * bufnext;
+        if (it >= BATCH_NBUF) bulk_wait_read<BATCH_NBUF - 1>();
+        const u64 left = count - j0;
+        const int cnt = left < (u64)opt ? (int)left : opt;
+        if (cnt == opt) {
+            for (int c = 0; c < chunks; ++c) {
+                u32 w[4];
+                gen16<G, DT>(e, w);
+                st_shared_v4(buf + (u32)c * 16u, w[0], w[1], w[2], w[3]);
+            }
+        } else {
+            for (int c = 0; c * PER < cnt; ++c) {
+                u32 w[4];
+                gen16_partial<G, DT>(e, w, cnt - c * PER);
+                st_shared_v4(buf + (u32)c * 16u, w[0], w[1], w[2], w[3]);
+            }
+        }
+        fence_proxy_async_shared();
+        const u32 bytes = (u32)cnt * ES, full = bytes & ~15u;
+        unsigned char *dst = out + j0 * ES;
+        if (full) {
+            bulk_store_s2g(dst, buf, full);
+            bulk_commit();
+        }
+        for (u32 b = full; b < bytes; b += ES) {
+            if (ES == 8) *reinterpret_cast<u64 *>(dst + b) = lds_u64(buf + b);
+            else *reinterpret_cast<u32 *>(dst + b) = lds_u32(buf + b);
+        }
+    }
+    bulk_wait_read<0>();
+    if (slot) store_state(e, slot);
+}
+
+#define XR_BATCH_CASE(V, DT)                                                              \
+    case (V) * 4 + (DT):                                                                  \
+        batch_lane<V, DT>(st, slot, out, count, buf0, bufnext, d.opt);                    \
+        break;
+
+__global__ void __launch_bounds__(512) k_batch_fill(BatchDev d)
+{
+    extern __shared__ __align__(16) unsigned char bsmem[];
+    const int lane = threadIdx.x & 31;
+    const u32 buf0 = smem_addr(bsmem) + threadIdx.x * d.bufstride;
+    const u32 bufnext = blockDim.x * d.bufstride;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(d.counter, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= d.ntasks) break;
+        const u64 code = d.tasks[t];
+        const BGroup g = d.groups[code >> 40];
+        const u64 s = (code & ((1ull << 40) - 1)) * 32 + (u64)lane;
+        if (s >= g.nseg) continue;
+        const u64 *pre = d.prefix + g.prefix_first;
+        u32 lo = 0, hi = g.nreq;  // pre[lo] <= s < pre[hi]
+        while (hi - lo > 1) {
+            const u32 mid = (lo + hi) >> 1;
+            if (pre[mid] <= s) lo = mid;
+            else hi = mid;
+        }
+        const BReq q = d.reqs[d.group_reqs[g.req_first + lo]];
+        const u64 seg = s - pre[lo];
+        const u64 start = seg << BSEG_LOG2;
+        const u64 count = (q.n - start) < BSEG ? (q.n - start) : BSEG;
+        const u32 *st = d.segstates + (q.seg_base + seg) * SLOT_WORDS;
+        unsigned char *slot = (start + count == q.n) ? d.slots + q.slot * 32 : nullptr;
+        const int es = (g.dtype == DT_U64 || g.dtype == DT_F64) ? 8 : 4;
+        unsigned char *out = d.out + q.out_offset + start * (u64)es;
+        switch (g.variant * 4 + g.dtype) {
+            XR_BATCH_CASE(0, DT_U64) XR_BATCH_CASE(0, DT_F64) XR_BATCH_CASE(0, DT_F32)
+            XR_BATCH_CASE(1, DT_U64) XR_BATCH_CASE(1, DT_F64) XR_BATCH_CASE(1, DT_F32)
+            XR_BATCH_CASE(2, DT_U64) XR_BATCH_CASE(2, DT_F64) XR_BATCH_CASE(2, DT_F32)
+            XR_BATCH_CASE(3, DT_U64) XR_BATCH_CASE(3, DT_F64) XR_BATCH_CASE(3, DT_F32)
+            XR_BATCH_CASE(4, DT_U64) XR_BATCH_CASE(4, DT_F64) XR_BATCH_CASE(4, DT_F32)
+            XR_BATCH_CASE(5, DT_U64) XR_BATCH_CASE(5, DT_F64) XR_BATCH_CASE(5, DT_F32)
+            XR_BATCH_CASE(6, DT_U32) XR_BATCH_CASE(6, DT_F64) XR_BATCH_CASE(6, DT_F32)
+            XR_BATCH_CASE(7, DT_U32) XR_BATCH_CASE(7, DT_F64) XR_BATCH_CASE(7, DT_F32)
+            XR_BATCH_CASE(8, DT_U32) XR_BATCH_CASE(8, DT_F64) XR_BATCH_CASE(8, DT_F32)
+        default:
+            break;
+        }
+    }
+    bulk_wait_all<0>();
+}
+#undef XR_BATCH_CASE
+
+}  // namespace xr
+
+using namespace xr;
+
+// ---------------------------------------------------------------- host side
+
+struct xr_batch {
+    xr_ctx *ctx;
+    size_t nreq;
+    u64 arena_bytes, ntasks, nseg_total;
+    // device plan
+    BReq *d_reqs;
+    BGroup *d_groups;
+    u32 *d_group_reqs;
+    u64 *d_prefix, *d_tasks;
+    unsigned long long *d_counter;
+    u32 *d_segstates;
+    BLevelItem *d_items;              // all level lists, concatenated
+    struct LevelLaunch {
+        int engine, level;
+        size_t first, count;
+    };
+    std::vector<LevelLaunch> levels;
+    // configuration
+    int opt, block;
+    // graph cache
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    const void *g_seeds, *g_slots, *g_out;
+    int g_opt, g_block;
+    cudaStream_t cap;
+    void *d_slot_backup;
+    size_t slot_backup_bytes;
+    size_t max_slot;
+};
+
+static int engine_of_variant(int v) { return v <= 2 ? 0 : (v == 4 ? 2 : (v <= 5 ? 1 : 3)); }
+static int es_of(int dtype) { return (dtype == XR_U64 || dtype == XR_F64) ? 8 : 4; }
+static bool dtype_ok_b(int v, int dt)
+{
+    if (dt == XR_F64 || dt == XR_F32) return true;
+    if (dt == XR_U64) return v <= 5;
+    if (dt == XR_U32) return v >= 6;
+    return false;
+}
+
+static int st_of(cudaError_t e)
+{
+    if (e == cudaSuccess) return XR_OK;
+    if (e == cudaErrorMemoryAllocation) return XR_ENOMEM;
+    return XR_ECUDA;
+}
+
+static u32 bufstride_for(int opt) { return (u32)(opt * 8 + 16); }
+static size_t smem_for(int opt, int block) { return (size_t)BATCH_NBUF * block * bufstride_for(opt); }
+
+extern "C" int xr_batch_destroy(xr_batch *b)
+{
+    if (!b) return XR_OK;
+    cudaSetDevice(b->ctx->device);
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->d_reqs);
+    cudaFree(b->d_groups);
+    cudaFree(b->d_group_reqs);
+    cudaFree(b->d_prefix);
+    cudaFree(b->d_tasks);
+    cudaFree(b->d_counter);
+    cudaFree(b->d_segstates);
+    cudaFree(b->d_items);
+    cudaFree(b->d_slot_backup);
+    delete b;
+    return XR_OK;
+}
+
+template <typename T>
+static cudaError_t upload(T **dst, const std::vector<T> &src)
+{
+    *dst = nullptr;
+    if (src.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)dst, src.size() * sizeof(T));
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+extern "C" int xr_batch_create(xr_ctx *ctx, const xr_request *h_reqs, size_t nreq, xr_batch **out)
+{
+    if (!ctx || !out || (nreq && !h_reqs)) return XR_EINVAL;
+    *out = nullptr;
+    // checks
+    std::vector<u64> slots_seen;
+    slots_seen.reserve(nreq);
+    for (size_t r = 0; r < nreq; ++r) {
+        const xr_request &q = h_reqs[r];
+        if (q.variant < 0 || q.variant >= XR_NUM_VARIANTS || !dtype_ok_b(q.variant, q.dtype)) return XR_EINVAL;
+        if (q.out_offset % 16) return XR_EINVAL;
+        if (q.n > (1ull << 50)) return XR_EINVAL;
+        slots_seen.push_back(q.slot);
+    }
+    std::sort(slots_seen.begin(), slots_seen.end());
+    for (size_t i = 1; i < slots_seen.size(); ++i)
+        if (slots_seen[i] == slots_seen[i - 1]) return XR_EINVAL;
+
+    xr_batch *b = new xr_batch();  // value-initialized: every plain member starts at zero
+    b->ctx = ctx;
+    b->nreq = nreq;
+    b->opt = 16;
+    b->block = 256;
+    b->max_slot = slots_seen.empty() ? 0 : (size_t)slots_seen.back();
+
+    // requests and segment bases
+    std::vector<BReq> reqs(nreq);
+    u64 segs = 0, arena = 0;
+    for (size_t r = 0; r < nreq; ++r) {
+        const xr_request &q = h_reqs[r];
+        reqs[r].n = q.n;
+        reqs[r].out_offset = q.out_offset;
+        reqs[r].slot = q.slot;
+        reqs[r].seg_base = segs;
+        reqs[r].variant = q.variant;
+        reqs[r].dtype = q.dtype;
+        segs += (q.n + BSEG - 1) / BSEG;
+        arena = std::max<u64>(arena, q.out_offset + q.n * (u64)es_of(q.dtype));
+    }
+    b->nseg_total = segs;
+    b->arena_bytes = arena;
+
+    // groups by (variant, dtype)
+    std::vector<BGroup> groups;
+    std::vector<u32> group_reqs;
+    std::vector<u64> prefix;
+    struct TaskKey {
+        u64 code;
+        u64 len;  // longest lane of the task
+    };
+    std::vector<TaskKey> tasks;
+    for (int v = 0; v < XR_NUM_VARIANTS; ++v)
+        for (int dt = 0; dt < 4; ++dt) {
+            std::vector<u32> members;
+            for (size_t r = 0; r < nreq; ++r)
+                if (reqs[r].variant == v && reqs[r].dtype == dt && reqs[r].n > 0) members.push_back((u32)r);
+            if (members.empty()) continue;
+            BGroup g;
+            g.variant = v;
+            g.dtype = dt;
+            g.nreq = (u32)members.size();
+            g.req_first = (u32)group_reqs.size();
+            g.prefix_first = prefix.size();
+            u64 acc = 0;
+            std::vector<u64> seglen;  // length of every segment of the group, in order
+            for (u32 r : members) {
+                group_reqs.push_back(r);
+                prefix.push_back(acc);
+                const u64 P = (reqs[r].n + BSEG - 1) / BSEG;
+                for (u64 q = 0; q < P; ++q) seglen.push_back(std::min<u64>(BSEG, reqs[r].n - q * BSEG));
+                acc += P;
+            }
+            prefix.push_back(acc);
+            g.nseg = acc;
+            const u64 gi = groups.size();
+            groups.push_back(g);
+            for (u64 t = 0; t * 32 < acc; ++t) {
+                u64 len = 0;
+                for (u64 s = t * 32; s < std::min<u64>(acc, t * 32 + 32); ++s) len = std::max(len, seglen[s]);
+                tasks.push_back({(gi << 40) | t, len});
+            }
+        }
+    // longest tasks first: short ones fill the tail of the persistent grid
+    std::stable_sort(tasks.begin(), tasks.end(), [](const TaskKey &a, const TaskKey &c) { return a.len > c.len; });
+    std::vector<u64> task_codes(tasks.size());
+    for (size_t i = 0; i < tasks.size(); ++i) task_codes[i] = tasks[i].code;
+    b->ntasks = task_codes.size();
+
+    // level lists per (engine, level) of the segment-start scheme
+    std::vector<BLevelItem> items;
+    for (int l = PSET_LEVELS - 1; l >= 0; --l) {
+        const u64 stride = 1ull << (PSET_BITS * l), span = stride << PSET_BITS;
+        for (int e = 0; e < NUM_ENGINES; ++e) {
+            xr_batch::LevelLaunch L;
+            L.engine = e;
+            L.level = l;
+            L.first = items.size();
+            for (size_t r = 0; r < nreq; ++r) {
+                if (engine_of_variant(reqs[r].variant) != e) continue;
+                const u64 P = (reqs[r].n + BSEG - 1) / BSEG;
+                if (P <= stride) continue;
+                for (u64 p = 0; p * span < P; ++p) items.push_back({reqs[r].seg_base + p * span, reqs[r].seg_base + P});
+            }
+            L.count = items.size() - L.first;
+            if (L.count) b->levels.push_back(L);
+        }
+    }
+
+    cudaError_t err = cudaSetDevice(ctx->device);
+    if (err == cudaSuccess) err = upload(&b->d_reqs, reqs);
+    if (err == cudaSuccess) err = upload(&b->d_groups, groups);
+    if (err == cudaSuccess) err = upload(&b->d_group_reqs, group_reqs);
+    if (err == cudaSuccess) err = upload(&b->d_prefix, prefix);
+    if (err == cudaSuccess) err = upload(&b->d_tasks, task_codes);
+    if (err == cudaSuccess) err = upload(&b->d_items, items);
+    if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_counter, sizeof(unsigned long long));
+    if (err == cudaSuccess && segs) err = cudaMalloc((void **)&b->d_segstates, segs * 32);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (err == cudaSuccess) {
+        static bool attr = false;
+        if (!attr) {
+            err = cudaFuncSetAttribute(k_batch_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            attr = (err == cudaSuccess);
+        }
+    }
+    if (err != cudaSuccess) {
+        xr_batch_destroy(b);
+        return st_of(err);
+    }
+    *out = b;
+    return XR_OK;
+}
+
+extern "C" uint64_t xr_batch_arena_bytes(const xr_batch *b) { return b ? b->arena_bytes : 0; }
+extern "C" uint64_t xr_batch_tasks(const xr_batch *b) { return b ? b->ntasks : 0; }
+
+extern "C" int xr_batch_set_config(xr_batch *b, int opt, int block)
+{
+    if (!b) return XR_EINVAL;
+    if (opt != 4 && opt != 8 && opt != 16 && opt != 32 && opt != 64) return XR_EINVAL;
+    if (block != 128 && block != 256 && block != 512) return XR_EINVAL;
+    if (smem_for(opt, block) > 227 * 1024) return XR_EINVAL;
+    b->opt = opt;
+    b->block = block;
+    return XR_OK;
+}
+
+extern "C" int xr_batch_get_config(const xr_batch *b, int *opt, int *block)
+{
+    if (!b || !opt || !block) return XR_EINVAL;
+    *opt = b->opt;
+    *block = b->block;
+    return XR_OK;
+}
+
+// Enqueue one run on `st` (not captured, or being captured).
+static cudaError_t enqueue_run(xr_batch *b, const uint64_t *d_seeds, void *d_slots, void *d_out, cudaStream_t st)
+{
+    xr_ctx *ctx = b->ctx;
+    BatchDev d;
+    d.reqs = b->d_reqs;
+    d.groups = b->d_groups;
+    d.group_reqs = b->d_group_reqs;
+    d.prefix = b->d_prefix;
+    d.tasks = b->d_tasks;
+    d.ntasks = b->ntasks;
+    d.counter = b->d_counter;
+    d.segstates = b->d_segstates;
+    d.slots = (unsigned char *)d_slots;
+    d.out = (unsigned char *)d_out;
+    d.seeds = reinterpret_cast<const u64 *>(d_seeds);
+    d.status = ctx->d_status;
+    d.opt = b->opt;
+    d.bufstride = bufstride_for(b->opt);
+    cudaError_t err = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st);
+    if (err != cudaSuccess || b->nreq == 0) return err;
+    k_batch_seed<<<(unsigned)((b->nreq + 127) / 128), 128, 0, st>>>(d, b->nreq);
+    count_launch();
+    err = cudaGetLastError();
+    for (size_t i = 0; i < b->levels.size() && err == cudaSuccess; ++i) {
+        const xr_batch::LevelLaunch &L = b->levels[i];
+        const int di = pset_index(L.engine, BSEG_LOG2);
+        const int n = engine_bits(L.engine);
+        const size_t set_words = (size_t)PSET_SIZE * n * (n / 32);
+        const uint32_t *P = pset_sets(ctx, L.engine, di) + (size_t)L.level * set_words;
+        const dim3 grid((unsigned)((L.count + 255) / 256), PSET_SIZE - 1);
+        const u64 stride = 1ull << (PSET_BITS * L.level);
+        if (n == 256)
+            k_batch_level<8><<<grid, 256, 0, st>>>(P, b->d_items + L.first, L.count, stride, b->d_segstates);
+        else
+            k_batch_level<4><<<grid, 256, 0, st>>>(P, b->d_items + L.first, L.count, stride, b->d_segstates);
+        count_launch();
+        err = cudaGetLastError();
+    }
+    if (err != cudaSuccess || b->ntasks == 0) return err;
+    int per_sm = 0, sms = 0;
+    const size_t smem = smem_for(b->opt, b->block);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_fill, b->block, smem);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    u64 grid = (u64)per_sm * sms;
+    const u64 warps_needed = b->ntasks, warps_per_block = (u64)b->block / 32;
+    grid = std::min<u64>(grid, (warps_needed + warps_per_block - 1) / warps_per_block);
+    k_batch_fill<<<(unsigned)grid, b->block, smem, st>>>(d);
+    count_launch();
+    return cudaGetLastError();
+}
+
+extern "C" int xr_batch_run(xr_batch *b, const uint64_t *d_seeds, void *d_slots, void *d_out, int use_graph,
+                            void *stream)
+{
+    if (!b) return XR_EINVAL;
+    if (b->nreq == 0) return XR_OK;
+    if (!d_slots || ((uintptr_t)d_slots % 16)) return XR_EINVAL;
+    if (b->arena_bytes && (!d_out || ((uintptr_t)d_out % 16))) return XR_EINVAL;
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (!use_graph) return st_of(enqueue_run(b, d_seeds, d_slots, d_out, st));
+    if (!b->exec || b->g_seeds != d_seeds || b->g_slots != d_slots || b->g_out != d_out || b->g_opt != b->opt ||
+        b->g_block != b->block) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        cudaError_t err = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (err != cudaSuccess) return st_of(err);
+        cudaError_t e1 = enqueue_run(b, d_seeds, d_slots, d_out, b->cap);
+        err = cudaStreamEndCapture(b->cap, &b->graph);
+        if (e1 != cudaSuccess) return st_of(e1);
+        if (err != cudaSuccess) return st_of(err);
+        err = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (err != cudaSuccess) return st_of(err);
+        b->g_seeds = d_seeds;
+        b->g_slots = d_slots;
+        b->g_out = d_out;
+        b->g_opt = b->opt;
+        b->g_block = b->block;
+    }
+    return st_of(cudaGraphLaunch(b->exec, st));
+}
+
+extern "C" int xr_batch_tune(xr_batch *b, const uint64_t *d_seeds, void *d_slots, void *d_out, void *stream,
+                             float *best_ms)
+{
+    if (!b || !d_slots) return XR_EINVAL;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const size_t nbytes = (b->max_slot + 1) * 32;
+    cudaError_t err = cudaSuccess;
+    if (b->slot_backup_bytes < nbytes) {
+        cudaFree(b->d_slot_backup);
+        b->d_slot_backup = nullptr;
+        err = cudaMalloc(&b->d_slot_backup, nbytes);
+        if (err != cudaSuccess) return st_of(err);
+        b->slot_backup_bytes = nbytes;
+    }
+    err = cudaMemcpyAsync(b->d_slot_backup, d_slots, nbytes, cudaMemcpyDeviceToDevice, st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int opts[5] = {4, 8, 16, 32, 64}, blocks[3] = {128, 256, 512};
+    float best = 1e30f;
+    int bo = b->opt, bb = b->block;
+    for (int oi = 0; oi < 5 && err == cudaSuccess; ++oi)
+        for (int bi = 0; bi < 3 && err == cudaSuccess; ++bi) {
+            if (smem_for(opts[oi], blocks[bi]) > 227 * 1024) continue;
+            b->opt = opts[oi];
+            b->block = blocks[bi];
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+                err = cudaMemcpyAsync(d_slots, b->d_slot_backup, nbytes, cudaMemcpyDeviceToDevice, st);
+                if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+                if (err == cudaSuccess) err = enqueue_run(b, d_seeds, d_slots, d_out, st);
+                if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                float t = 0;
+                if (err == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms = std::min(ms, t);  // first repetition warms up
+            }
+            if (err == cudaSuccess && ms < best) {
+                best = ms;
+                bo = opts[oi];
+                bb = blocks[bi];
+            }
+        }
+    b->opt = bo;
+    b->block = bb;
+    if (err == cudaSuccess) err = cudaMemcpyAsync(d_slots, b->d_slot_backup, nbytes, cudaMemcpyDeviceToDevice, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms) *best_ms = best;
+    return st_of(err);
+}

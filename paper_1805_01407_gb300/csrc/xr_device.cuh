@@ -171,23 +171,25 @@ static __device__ __noinline__ u64 unit_f64_bits_small(u64 x)
     return ((u64)(p + 970) << 52) | frac;
 }
 
-// Common path, high word hi != 0 with lz = clz(hi) <= 31.  Clearing the 11 low
-// bits of x and shifting left by lz puts the leading one of x >> 11 at bit 63;
-// bits 63..11 of that are the 53-bit significand, leading one at bit 52.  The
-// value is 1.f * 2^(-1 - lz): biased exponent 1022 - lz; since the leading one
-// (bit 20 of the high word) already adds one to the exponent field, adding
-// (1021 - lz) << 20 to the high word completes the encoding.
+// Common path, high word hi != 0 with lz = clz(hi) <= 31: v = x >> 11 has its
+// leading one at bit 52 - lz, so v << lz puts it at bit 52 (bit 20 of the high
+// word) and its low 52 bits are the fraction.  The value is 1.f * 2^(-1 - lz):
+// biased exponent 1022 - lz, and since the leading one already adds one to the
+// exponent field, adding (1021 - lz) << 20 to the high word completes the
+// encoding.  Seven integer operations; the rare x < 2^32 branches out of line.
 __device__ __forceinline__ u64 unit_f64_bits(u64 x)
 {
-    const u32 hi = (u32)(x >> 32);
+    u32 lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(x));
     if (__builtin_expect(hi == 0u, 0)) return unit_f64_bits_small(x);
-    const u32 lo = (u32)x & 0xFFFFF800u;
+    const u32 vl = __funnelshift_r(lo, hi, 11);
+    const u32 vh = hi >> 11;
     const int lz = __clz(hi);
-    const u32 yh = __funnelshift_l(lo, hi, lz);
-    const u32 yl = lo << lz;
-    const u32 mh = (yh >> 11) + ((u32)(1021 - lz) << 20);
-    const u32 ml = __funnelshift_r(yl, yh, 11);
-    return ((u64)mh << 32) | ml;
+    const u32 mh = __funnelshift_l(vl, vh, lz) + ((u32)(1021 - lz) << 20);
+    const u32 ml = vl << lz;
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(ml), "r"(mh));
+    return r;
 }
 
 // x * 2^-32 as binary64 bits for a 32-bit word: leading one at bit p = 31 - lz,
@@ -215,6 +217,61 @@ __device__ __forceinline__ typename OutElem<DT>::type convert(W x)
     if (DT == DT_U64 || DT == DT_U32) return (typename OutElem<DT>::type)x;
     if (DT == DT_F64) return (typename OutElem<DT>::type)unit_f64_bits(x);
     return (typename OutElem<DT>::type)unit_f32_bits(x);
+}
+
+// ---------------------------------------------------------------- output words
+// Next 16 bytes of output elements (2 x 8 B or 4 x 4 B), stepping the engine.
+template <typename G, int DT>
+__device__ __forceinline__ void gen16(typename G::E &e, u32 (&w)[4])
+{
+    typedef typename OutElem<DT>::type OT;
+    if (sizeof(OT) == 8) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const u64 o = (u64)convert<DT>(G::out(e));
+            e.step();
+            w[2 * q] = (u32)o;
+            w[2 * q + 1] = (u32)(o >> 32);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            w[q] = (u32)convert<DT>(G::out(e));
+            e.step();
+        }
+    }
+}
+
+// Same for the last, partial tile: only `cnt` more outputs are taken.
+template <typename G, int DT>
+__device__ __forceinline__ void gen16_partial(typename G::E &e, u32 (&w)[4], int cnt)
+{
+    typedef typename OutElem<DT>::type OT;
+    constexpr int PER = 16 / (int)sizeof(OT);
+    w[0] = w[1] = w[2] = w[3] = 0u;
+    for (int q = 0; q < PER && q < cnt; ++q) {
+        const u64 o = (u64)convert<DT>(G::out(e));
+        e.step();
+        if (sizeof(OT) == 8) {
+            w[2 * q] = (u32)o;
+            w[2 * q + 1] = (u32)(o >> 32);
+        } else {
+            w[q] = (u32)o;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- seeding
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014; Sec. 5.3): Weyl sequence with
+// increment 0x9e3779b97f4a7c15, then the 64-bit mixer (shifts 30, 27, 31;
+// multipliers 0xbf58476d1ce4e5b9, 0x94d049bb133111eb).
+__device__ __forceinline__ u64 splitmix64_next(u64 &x)
+{
+    x += 0x9e3779b97f4a7c15ull;
+    u64 z = x;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
 }
 
 // ---------------------------------------------------------------- F2 algebra

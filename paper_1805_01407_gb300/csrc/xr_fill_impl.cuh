@@ -24,47 +24,6 @@ constexpr int FILL_NBUF = 2;           // shared-memory tiles per warp
 constexpr int TILE_BYTES = 32 * 128;   // 32 rows x 128 bytes
 constexpr int FILL_SMEM = FILL_WARPS * FILL_NBUF * TILE_BYTES + 1024;  // + alignment slack
 
-// Next 16 bytes of output elements (2 x 8 B or 4 x 4 B), stepping the engine.
-template <typename G, int DT>
-__device__ __forceinline__ void gen16(typename G::E &e, u32 (&w)[4])
-{
-    typedef typename OutElem<DT>::type OT;
-    if (sizeof(OT) == 8) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const u64 o = (u64)convert<DT>(G::out(e));
-            e.step();
-            w[2 * q] = (u32)o;
-            w[2 * q + 1] = (u32)(o >> 32);
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            w[q] = (u32)convert<DT>(G::out(e));
-            e.step();
-        }
-    }
-}
-
-// Same for the last, partial tile: only `cnt` more outputs are taken.
-template <typename G, int DT>
-__device__ __forceinline__ void gen16_partial(typename G::E &e, u32 (&w)[4], int cnt)
-{
-    typedef typename OutElem<DT>::type OT;
-    constexpr int PER = 16 / (int)sizeof(OT);
-    w[0] = w[1] = w[2] = w[3] = 0u;
-    for (int q = 0; q < PER && q < cnt; ++q) {
-        const u64 o = (u64)convert<DT>(G::out(e));
-        e.step();
-        if (sizeof(OT) == 8) {
-            w[2 * q] = (u32)o;
-            w[2 * q + 1] = (u32)(o >> 32);
-        } else {
-            w[q] = (u32)o;
-        }
-    }
-}
-
 // Generate one 32 x 128 B tile row for this lane into the swizzled tile:
 // 16-byte chunk c of row r lives at r * 128 + ((c ^ (r & 7)) * 16), so the 8
 // lanes of each quarter-warp hit 8 different bank groups.

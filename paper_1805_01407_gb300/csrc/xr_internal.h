@@ -18,6 +18,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 // Count one kernel launch (host-side, process-wide).
 void count_launch();
 
+// Number of engines (xoshiro256, xoroshiro128, xoroshiro128 for ++, xoshiro128).
+constexpr int NUM_ENGINES_H = 4;
+
 // Engine of each variant and its state size in bits.
 int engine_of(int variant);
 int engine_bits(int engine);
@@ -63,4 +66,31 @@ cudaError_t launch_streams_psets(int engine, const uint32_t *sets3, void *states
 cudaError_t launch_seed(int variant, const uint64_t *d_seeds, uint64_t seed, size_t count,
                         void *states, int *status, cudaStream_t stream);
 
+}  // namespace xr
+
+// Jump distances with power sets, per engine: jump, long jump, xr_fill_seq segment.
+static const int NUM_PSET_DISTS = 3;
+
+// The context (opaque in include/xr.h).
+struct xr_ctx {
+    int device;
+    uint32_t *tables[xr::NUM_ENGINES_H];
+    uint32_t *psets[xr::NUM_ENGINES_H];  // NUM_PSET_DISTS x PSET_LEVELS power sets
+    int *d_status;
+    void *scratch;            // segment start states of xr_fill_seq
+    size_t scratch_bytes;
+    void *staging[2];         // output staging of xr_fill_host
+    void *chunk_states[2];    // stream start states of xr_fill_host
+    void *base_state;         // one state (xr_fill_host)
+    size_t staging_bytes, chunk_states_bytes;
+    cudaStream_t side;        // copy stream of xr_fill_host
+    cudaEvent_t ev_gen[2], ev_copy[2];
+    xr::EncodeTiledFn encode;
+};
+
+namespace xr {
+// Index of the power sets of distance log2 d for an engine (-1 if none).
+int pset_index(int engine, int d);
+// The three level sets of distance index di of an engine.
+const uint32_t *pset_sets(const xr_ctx *ctx, int engine, int di);
 }  // namespace xr

@@ -329,18 +329,6 @@ cudaError_t launch_streams_psets(int engine, const uint32_t *sets3, void *states
 
 // ---------------------------------------------------------------- seeding
 
-// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014; Sec. 5.3): Weyl sequence with
-// increment 0x9e3779b97f4a7c15, then the 64-bit mixer (shifts 30, 27, 31;
-// multipliers 0xbf58476d1ce4e5b9, 0x94d049bb133111eb).
-__device__ __forceinline__ u64 splitmix64_next(u64 &x)
-{
-    x += 0x9e3779b97f4a7c15ull;
-    u64 z = x;
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-    return z ^ (z >> 31);
-}
-
 // WORDBYTES = 8: state word j = output j.  WORDBYTES = 4: output t gives words
 // 2t (low half) and 2t + 1 (high half).
 template <int WORDBYTES, int K>

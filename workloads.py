@@ -63,3 +63,23 @@ def random_states(k: int, w: int, count: int, seed: int) -> np.ndarray:
     zero = ~out.any(axis=1)
     out[zero, 0] = 1
     return out
+
+
+# Batched uneven requests: 4096 requests, request r seeded with SplitMix64(r),
+# generator uniform over the 8 bulk generators, length log-uniform in
+# [1, 2^24], output type uniform over {native word, double}.
+CONFIG_BATCH = dict(nreq=4096, max_len=1 << 24, mix_seed=4)
+
+
+def batch_requests(nreq=4096, max_len=1 << 24, mix_seed=4, variants=BULK_VARIANTS):
+    """[(variant, dtype, n, seed)] for the batched configuration."""
+    rng = np.random.default_rng(mix_seed)
+    v = rng.integers(0, len(variants), size=nreq)
+    dt = rng.integers(0, 2, size=nreq)
+    n = np.floor(np.exp(rng.uniform(0.0, np.log(max_len + 1.0), size=nreq))).astype(np.int64)
+    n = np.clip(n, 1, max_len)
+    out = []
+    for r in range(nreq):
+        name = variants[int(v[r])]
+        out.append((name, native_dtype(name) if dt[r] == 0 else "f64", int(n[r]), r))
+    return out
