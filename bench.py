@@ -49,12 +49,14 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-steps", type=int, default=5)
-    p.add_argument("--profile", choices=["fill", "streams"], default=None,
+    p.add_argument("--profile", choices=["fill", "streams", "batch"], default=None,
                    help="run a small case for an ncu capture instead of the benchmark")
     p.add_argument("--profile-variant", default="xoshiro256**")
     p.add_argument("--profile-dtype", default=None)
     p.add_argument("--profile-streams", type=int, default=1 << 16)
     p.add_argument("--profile-launches", type=int, default=3)
+    p.add_argument("--profile-max-len", type=int, default=1 << 24,
+                   help="batch profile: largest request length")
     return p.parse_args()
 
 
@@ -489,6 +491,8 @@ def run_profile(args):
     import paper_1805_01407_gb300 as xr
     from paper_1805_01407_gb300 import build as libbuild
     libbuild.build()
+    if args.profile == "batch":
+        return run_profile_batch(args)
     v = args.profile_variant
     d = args.profile_dtype or W.native_dtype(v)
     S, m = args.profile_streams, W.CONFIG_BULK["m"]
@@ -506,6 +510,31 @@ def run_profile(args):
         torch.cuda.synchronize()
         assert ctx.status() == 0
     print("profile case done: %s %s S=%d m=%d" % (args.profile, v, S, m))
+    return 0
+
+
+def run_profile_batch(args):
+    """Batched configuration (max length --profile-max-len) run without a graph,
+    one warm-up and --profile-launches timed-free runs, for ncu."""
+    import torch
+    import paper_1805_01407_gb300 as xr
+    from paper_1805_01407_gb300 import build as libbuild
+    libbuild.build()
+    specs = W.batch_requests(nreq=W.CONFIG_BATCH["nreq"], max_len=args.profile_max_len,
+                             mix_seed=W.CONFIG_BATCH["mix_seed"])
+    with xr.Context(0) as ctx:
+        reqs, offs, arena = xr.pack_requests([(v, dt, n, r) for r, (v, dt, n, _) in enumerate(specs)])
+        b = xr.Batch(ctx, reqs)
+        b.set_config(32, 128)
+        slots = torch.zeros(len(specs) * 32, dtype=torch.uint8, device="cuda")
+        out = torch.empty(arena, dtype=torch.uint8, device="cuda")
+        seeds = torch.tensor([s for (_, _, _, s) in specs], dtype=torch.int64, device="cuda")
+        for _ in range(1 + args.profile_launches):
+            b.run(seeds, slots, out)
+        torch.cuda.synchronize()
+        assert ctx.status() == 0
+        b.close()
+    print("profile case done: batch of %d requests, %.2f GB" % (len(specs), arena / 1e9))
     return 0
 
 

@@ -309,20 +309,25 @@ class Context:
         return buf.raw
 
 
-def pack_requests(specs, align=256):
+def pack_requests(specs, align=None):
     """Lay out requests in one output arena.
 
     specs: iterable of (variant, dtype, n[, slot]); slot defaults to the
     request's index.  Returns (list of Request, list of byte offsets, arena
-    bytes); every request starts on an `align`-byte boundary."""
+    bytes).  By default every request starts on a boundary of 1024 of its
+    elements, which lets the batch write whole 1024-output segments with
+    tile stores; `align` (a multiple of 16) overrides that."""
     reqs, offs, off = [], [], 0
     for r, spec in enumerate(specs):
         v, dt, n = spec[0], spec[1], int(spec[2])
         slot = int(spec[3]) if len(spec) > 3 else r
+        a = align or 1024 * dtype_bytes(dt)
+        off = (off + a - 1) // a * a
         reqs.append(Request(_v(v), DTYPES[dt], n, slot, off))
         offs.append(off)
-        off += (n * dtype_bytes(dt) + align - 1) // align * align
-    return reqs, offs, off
+        off += n * dtype_bytes(dt)
+    a = align or 8192
+    return reqs, offs, (off + a - 1) // a * a
 
 
 class Batch:

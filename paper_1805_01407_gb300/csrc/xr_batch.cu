@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "xr_device.cuh"
+#include "xr_fill_impl.cuh"
 #include "xr_internal.h"
 
 namespace xr {
@@ -24,6 +25,7 @@ constexpr int BSEG_LOG2 = 10;            // outputs per segment = 1024
 constexpr u64 BSEG = 1ull << BSEG_LOG2;
 constexpr int BATCH_NBUF = 2;            // staged rows per lane
 constexpr int SLOT_WORDS = 8;            // 32-byte state slots
+constexpr int TILE_BYTES_B = 32 * 128;   // one 32-row x 128-byte tile
 
 struct BReq {
     u64 n, out_offset, slot, seg_base;
@@ -53,9 +55,13 @@ struct BatchDev {
     unsigned char *out;
     const u64 *seeds;
     int *status;
-    int opt;            // outputs per staged row
+    int opt;            // outputs per staged row (per-lane path)
     u32 bufstride;      // bytes between consecutive lanes' buffers
+    u32 warpbytes;      // shared memory per warp (1024-byte multiple)
+    int rows_ok;        // tensor maps over 1024-element rows are valid
 };
+
+constexpr u64 TASK_FULL = 1ull << 63;  // 32 full segments of one row-aligned request
 
 // ---------------------------------------------------------------- seeding / copy-in
 
@@ -218,26 +224,63 @@ __device__ __forceinline__ void batch_lane(const u32 *st, unsigned char *slot, u
     if (slot) store_state(e, slot);
 }
 
+// A warp whose 32 lanes hold 32 consecutive full segments of one request:
+// the segments are 32 consecutive 1024-element rows of the arena, written as
+// 32-row x 128-byte tiles by 2D TMA stores, exactly like the bulk fill.
+template <int V, int DT>
+__device__ __forceinline__ void batch_warp_rows(const u32 *st, unsigned char *slot, const CUtensorMap *map,
+                                                int row0, u32 tiles, int lane)
+{
+    typedef Gen<V> G;
+    typedef typename G::E E;
+    constexpr int COLS = 128 / (int)sizeof(typename OutElem<DT>::type);
+    E e;
+    load_state(e, st);
+    int it = 0;
+    for (int j0 = 0; j0 < (int)BSEG; j0 += COLS, ++it) {
+        const u32 tile = tiles + (u32)((it & 1) * TILE_BYTES_B);
+        if (it >= 2) {
+            if (lane == 0) bulk_wait_read<1>();
+            __syncwarp();
+        }
+        fill_tile_row<G, DT>(e, tile, lane, (size_t)COLS);
+        fence_proxy_async_shared();
+        __syncwarp();
+        if (lane == 0) {
+            tma_store_2d(map, tile, j0, row0);
+            bulk_commit();
+        }
+    }
+    if (lane == 0) bulk_wait_read<0>();
+    __syncwarp();
+    if (slot) store_state(e, slot);
+}
+
 #define XR_BATCH_CASE(V, DT)                                                              \
     case (V) * 4 + (DT):                                                                  \
-        batch_lane<V, DT>(st, slot, out, count, buf0, bufnext, d.opt);                    \
+        if (full) batch_warp_rows<V, DT>(st, slot, (DT == DT_U32 || DT == DT_F32) ? &map32 : &map64, row0, tiles, lane); \
+        else batch_lane<V, DT>(st, slot, out, count, buf0, bufnext, d.opt);               \
         break;
 
-__global__ void __launch_bounds__(512) k_batch_fill(BatchDev d)
+__global__ void __launch_bounds__(512)
+    k_batch_fill(BatchDev d, const __grid_constant__ CUtensorMap map64, const __grid_constant__ CUtensorMap map32)
 {
-    extern __shared__ __align__(16) unsigned char bsmem[];
-    const int lane = threadIdx.x & 31;
-    const u32 buf0 = smem_addr(bsmem) + threadIdx.x * d.bufstride;
-    const u32 bufnext = blockDim.x * d.bufstride;
+    extern __shared__ unsigned char bsmem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const u32 wbase = ((smem_addr(bsmem) + 1023u) & ~1023u) + (u32)warp * d.warpbytes;
+    const u32 tiles = wbase;                       // two 4 KiB tiles (full tasks)
+    const u32 buf0 = wbase + (u32)lane * d.bufstride;  // per-lane rows (other tasks)
+    const u32 bufnext = 32u * d.bufstride;
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(d.counter, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= d.ntasks) break;
         const u64 code = d.tasks[t];
-        const BGroup g = d.groups[code >> 40];
+        const bool full = (code & TASK_FULL) && d.rows_ok;
+        const BGroup g = d.groups[(code & ~TASK_FULL) >> 40];
         const u64 s = (code & ((1ull << 40) - 1)) * 32 + (u64)lane;
-        if (s >= g.nseg) continue;
+        if (s >= g.nseg) continue;  // never taken by full tasks
         const u64 *pre = d.prefix + g.prefix_first;
         u32 lo = 0, hi = g.nreq;  // pre[lo] <= s < pre[hi]
         while (hi - lo > 1) {
@@ -253,6 +296,7 @@ __global__ void __launch_bounds__(512) k_batch_fill(BatchDev d)
         unsigned char *slot = (start + count == q.n) ? d.slots + q.slot * 32 : nullptr;
         const int es = (g.dtype == DT_U64 || g.dtype == DT_F64) ? 8 : 4;
         unsigned char *out = d.out + q.out_offset + start * (u64)es;
+        const int row0 = (int)(q.out_offset / (BSEG * (u64)es) + seg - (u64)lane);
         switch (g.variant * 4 + g.dtype) {
             XR_BATCH_CASE(0, DT_U64) XR_BATCH_CASE(0, DT_F64) XR_BATCH_CASE(0, DT_F32)
             XR_BATCH_CASE(1, DT_U64) XR_BATCH_CASE(1, DT_F64) XR_BATCH_CASE(1, DT_F32)
@@ -325,7 +369,15 @@ static int st_of(cudaError_t e)
 }
 
 static u32 bufstride_for(int opt) { return (u32)(opt * 8 + 16); }
-static size_t smem_for(int opt, int block) { return (size_t)BATCH_NBUF * block * bufstride_for(opt); }
+// Per warp: two 32 x 128-byte tiles (full tasks) or 32 lanes x two staged
+// rows (other tasks), whichever is larger, in 1024-byte units.
+static u32 warpbytes_for(int opt)
+{
+    const u32 rows = (u32)BATCH_NBUF * 32u * bufstride_for(opt);
+    const u32 w = rows > 2u * TILE_BYTES_B ? rows : 2u * TILE_BYTES_B;
+    return (w + 1023u) & ~1023u;
+}
+static size_t smem_for(int opt, int block) { return (size_t)(block / 32) * warpbytes_for(opt) + 1024; }
 
 extern "C" int xr_batch_destroy(xr_batch *b)
 {
@@ -423,21 +475,31 @@ extern "C" int xr_batch_create(xr_ctx *ctx, const xr_request *h_reqs, size_t nre
             g.prefix_first = prefix.size();
             u64 acc = 0;
             std::vector<u64> seglen;  // length of every segment of the group, in order
+            std::vector<u32> segreq;  // its request
             for (u32 r : members) {
                 group_reqs.push_back(r);
                 prefix.push_back(acc);
                 const u64 P = (reqs[r].n + BSEG - 1) / BSEG;
-                for (u64 q = 0; q < P; ++q) seglen.push_back(std::min<u64>(BSEG, reqs[r].n - q * BSEG));
+                for (u64 q = 0; q < P; ++q) {
+                    seglen.push_back(std::min<u64>(BSEG, reqs[r].n - q * BSEG));
+                    segreq.push_back(r);
+                }
                 acc += P;
             }
+            const u64 rowbytes = BSEG * (u64)es_of(dt);
             prefix.push_back(acc);
             g.nseg = acc;
             const u64 gi = groups.size();
             groups.push_back(g);
             for (u64 t = 0; t * 32 < acc; ++t) {
                 u64 len = 0;
-                for (u64 s = t * 32; s < std::min<u64>(acc, t * 32 + 32); ++s) len = std::max(len, seglen[s]);
-                tasks.push_back({(gi << 40) | t, len});
+                const u64 s0 = t * 32, s1 = std::min<u64>(acc, t * 32 + 32);
+                bool full = (s1 - s0 == 32) && reqs[segreq[s0]].out_offset % rowbytes == 0;
+                for (u64 s = s0; s < s1; ++s) {
+                    len = std::max(len, seglen[s]);
+                    full = full && seglen[s] == BSEG && segreq[s] == segreq[s0];
+                }
+                tasks.push_back({(gi << 40) | t | (full ? TASK_FULL : 0ull), len});
             }
         }
     // longest tasks first: short ones fill the tail of the persistent grid
@@ -532,6 +594,31 @@ static cudaError_t enqueue_run(xr_batch *b, const uint64_t *d_seeds, void *d_slo
     d.status = ctx->d_status;
     d.opt = b->opt;
     d.bufstride = bufstride_for(b->opt);
+    d.warpbytes = warpbytes_for(b->opt);
+    // tensor maps over the arena as rows of 1024 elements (8- and 4-byte)
+    CUtensorMap maps[2];
+    memset(maps, 0, sizeof(maps));
+    d.rows_ok = 0;
+    if (ctx->encode && d_out && ((uintptr_t)d_out % 16) == 0) {
+        d.rows_ok = 1;
+        for (int k = 0; k < 2; ++k) {
+            const u64 es = k == 0 ? 8 : 4, rows = b->arena_bytes / (BSEG * es);
+            if (rows == 0) continue;
+            if (rows >= (1ull << 31)) {
+                d.rows_ok = 0;
+                continue;
+            }
+            const cuuint64_t dims[2] = {(cuuint64_t)BSEG, (cuuint64_t)rows};
+            const cuuint64_t strides[1] = {(cuuint64_t)(BSEG * es)};
+            const cuuint32_t box[2] = {(cuuint32_t)(128 / es), 32u};
+            const cuuint32_t estr[2] = {1u, 1u};
+            if (ctx->encode(&maps[k], k == 0 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2,
+                            d_out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                d.rows_ok = 0;
+        }
+    }
     cudaError_t err = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st);
     if (err != cudaSuccess || b->nreq == 0) return err;
     k_batch_seed<<<(unsigned)((b->nreq + 127) / 128), 128, 0, st>>>(d, b->nreq);
@@ -562,7 +649,7 @@ static cudaError_t enqueue_run(xr_batch *b, const uint64_t *d_seeds, void *d_slo
     u64 grid = (u64)per_sm * sms;
     const u64 warps_needed = b->ntasks, warps_per_block = (u64)b->block / 32;
     grid = std::min<u64>(grid, (warps_needed + warps_per_block - 1) / warps_per_block);
-    k_batch_fill<<<(unsigned)grid, b->block, smem, st>>>(d);
+    k_batch_fill<<<(unsigned)grid, b->block, smem, st>>>(d, maps[0], maps[1]);
     count_launch();
     return cudaGetLastError();
 }

@@ -145,11 +145,16 @@ def test_batch_tuner_keeps_results(ctx, xr):
     b.close()
 
 
-@pytest.mark.parametrize("opt,block", [(4, 128), (8, 512), (32, 256), (64, 128)])
-def test_batch_every_config(ctx, xr, opt, block):
+@pytest.mark.parametrize("opt,block,align", [(4, 128, None), (8, 512, None), (16, 256, 256), (32, 256, None),
+                                             (64, 128, 16)])
+def test_batch_every_config(ctx, xr, opt, block, align):
+    """Every tuner configuration, with requests placed on row boundaries (tile
+    stores for full segments) or only on 16/256-byte boundaries (per-lane
+    bulk copies everywhere)."""
     import torch
-    specs = small_mix(60, 3000, seed=25)
-    reqs, offs, arena = xr.pack_requests(specs)
+    specs = small_mix(60, 3000, seed=25) + [("xoshiro256**", "u64", 40000, 60), ("xoshiro128++", "f32", 70000, 61),
+                                            ("xoroshiro128+", "f64", 33 * 1024, 62)]
+    reqs, offs, arena = xr.pack_requests(specs, align=align)
     b = xr.Batch(ctx, reqs)
     b.set_config(opt, block)
     slots = torch.zeros(len(specs) * 32, dtype=torch.uint8, device="cuda")
