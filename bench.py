@@ -48,6 +48,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=20000)
     p.add_argument("--batched-steps", type=int, default=5)
     p.add_argument("--profile", choices=["fill", "streams", "batch"], default=None,
                    help="run a small case for an ncu capture instead of the benchmark")
@@ -368,6 +370,8 @@ def run_xr(args):
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if not args.no_batched:
         line["batched"] = run_batched(xr, ctx, args)
+    if not args.no_serve:
+        line["serving"] = run_serving(xr, ctx, args)
     if not args.no_e2e:
         line["e2e"] = run_e2e(ctx, args, first, bytes_per_step, world, dist)
     if dist:
@@ -440,6 +444,38 @@ def run_batched(xr, ctx, args):
         "tuned": {"outputs_per_row": opt, "block": block, "best_trial_ms": tune_ms},
         "tasks": b.tasks if False else None,
     }
+
+
+def run_serving(xr, ctx, args):
+    """Serving: 256 clients with device-resident states, Poisson arrivals at
+    20k requests/s, sizes log-uniform in [2^10, 2^26] values, u64/f64, 16 GiB
+    output budget; continuous batching against plain one-xr_fill_seq-per-request
+    under the same trace.  Then the same requests all at once (saturation)."""
+    import numpy as np
+    c = W.CONFIG_SERVE
+    names, seeds = W.serve_clients(c["nclients"])
+    arr, cl, n, dt = W.serve_trace(args.serve_requests, **c)
+    nbytes = float(sum(int(k) * (8 if d in ("u64", "f64") else 4) for k, d in zip(n, dt)))
+    res = {"workload": "256 clients (xoshiro256** / xoroshiro128++), Poisson 20k req/s, sizes log-uniform "
+                       "2^10..2^26, u64/f64, 16 GiB budget, %d requests (%.0f GB)" % (len(n), nbytes / 1e9)}
+    warm = W.serve_trace(64, **dict(c, trace_seed=99))
+    for mode in ("batched", "plain"):
+        with xr.Server(ctx, names, seeds, arena_bytes=c["arena_bytes"], mode=mode) as srv:
+            srv.replay(np.zeros(64), warm[1], warm[2], warm[3])
+            lat, wall = srv.replay(arr, cl, n, dt)
+            burst_lat, burst_wall = srv.replay(np.zeros(len(n) // 10), cl[: len(n) // 10], n[: len(n) // 10],
+                                               dt[: len(n) // 10])
+            st = srv.stats()
+        bb = float(sum(int(k) * 8 for k in n[: len(n) // 10]))
+        res[mode] = {"value": nbytes / (wall / 1e6) / 1e9, "unit": UNIT, "wall_ms": wall / 1e3,
+                     "latency_us_p50": float(np.percentile(lat, 50)), "latency_us_p99": float(np.percentile(lat, 99)),
+                     "saturation_value": bb / (burst_wall / 1e6) / 1e9,
+                     "saturation_latency_us_p99": float(np.percentile(burst_lat, 99)),
+                     "rounds": st["rounds"], "arena_peak_bytes": st["arena_peak"]}
+    res["value"] = res["batched"]["value"]
+    res["unit"] = UNIT
+    res["batched_vs_plain_saturation"] = res["batched"]["saturation_value"] / res["plain"]["saturation_value"]
+    return res
 
 
 def run_e2e(ctx, args, first, bytes_per_step, world, dist):

@@ -262,6 +262,69 @@ int xr_batch_get_config(const xr_batch *b, int *outputs_per_row, int *block);
 int xr_batch_tune(xr_batch *b, const uint64_t *d_seeds, void *d_slots, void *d_out, void *stream,
                   float *best_ms);
 
+/* ---- serving: continuous batching for many clients -------------------------
+ * A server owns, on the device, one generator state per client (seeded with
+ * SplitMix64 from a per-client seed) and an output arena of a fixed budget.
+ * Clients submit requests "the next n outputs of my sequence as dtype" at any
+ * time, from any thread.  A scheduler thread admits pending requests in
+ * arrival order while arena space (and a round slot) is free; at admission a
+ * small kernel gives each request its own start state (the client's state,
+ * after which the client's state jumps ahead by n), so a client's requests
+ * continue one sequence in submission order whatever runs concurrently.
+ * Admitted requests run as rounds of the batched kernels of xr_batch_*;
+ * up to max_rounds rounds are in flight on separate streams, so requests that
+ * arrive while others run are admitted and overlap on the device.  Outputs
+ * stay in the arena until released.  Plain mode instead runs one
+ * xr_fill_seq per request, in arrival order, on one stream (for comparison). */
+#define XR_SERVE_BATCHED 0
+#define XR_SERVE_PLAIN 1
+
+typedef struct {
+    uint64_t arena_bytes;          /* output budget (device memory the server allocates) */
+    uint32_t nclients;
+    uint32_t max_rounds;           /* rounds in flight (batched mode), >= 1 */
+    uint32_t max_round_requests;   /* requests per round (batched mode), >= 1 */
+    int mode;                      /* XR_SERVE_BATCHED or XR_SERVE_PLAIN */
+    int outputs_per_row, block;    /* batched kernel configuration; 0 = 16, 128 */
+} xr_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, released, rounds, bytes;
+    uint64_t arena_in_use, arena_peak;
+} xr_serve_stats;
+
+typedef struct xr_server xr_server;
+
+/* Create a server: h_client_variants / h_client_seeds have nclients entries
+ * (host).  Starts the scheduler thread.  XR_EINVAL on a bad config. */
+int xr_server_create(xr_ctx *ctx, const xr_server_config *cfg, const int *h_client_variants,
+                     const uint64_t *h_client_seeds, xr_server **out);
+/* Drop requests not yet admitted, wait for admitted ones, stop the
+ * scheduler and free everything. */
+int xr_server_destroy(xr_server *s);
+/* Queue a request (non-blocking).  XR_EINVAL for a bad client/dtype or a
+ * request larger than the whole arena. */
+int xr_server_submit(xr_server *s, uint32_t client, uint64_t n, int dtype, uint64_t *ticket);
+/* Block until the request is complete: its outputs are at byte *out_offset
+ * of the arena (xr_server_arena) until released; *latency_us is the time from
+ * submission to observed completion. */
+int xr_server_wait(xr_server *s, uint64_t ticket, uint64_t *out_offset, double *latency_us);
+/* Free a completed request's arena space (its outputs become invalid). */
+int xr_server_release(xr_server *s, uint64_t ticket);
+void *xr_server_arena(xr_server *s);
+/* Copy `bytes` of the arena at `offset` to dst (host or device memory, any
+ * kind) on `stream` and wait for the copy. */
+int xr_server_read(xr_server *s, uint64_t offset, uint64_t bytes, void *dst, void *stream);
+/* Current state of a client after every admitted request (waits for them). */
+int xr_server_client_state(xr_server *s, uint32_t client, void *h_words);
+int xr_server_stats(xr_server *s, xr_serve_stats *out);
+/* Load replay: submit request i at arrival_us[i] microseconds after the call
+ * starts (from the calling thread), release every output as soon as it
+ * completes, wait for all, and return each request's latency (us) and the
+ * wall time from the first arrival to the last completion. */
+int xr_server_replay(xr_server *s, const double *arrival_us, const uint32_t *clients, const uint64_t *ns,
+                     const int *dtypes, size_t nreq, double *latency_us, double *wall_us);
+
 /* ---- status and inspection ------------------------------------------------ */
 
 /* Sticky device status: XR_OK, or the first error a kernel recorded

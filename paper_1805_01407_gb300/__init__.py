@@ -35,6 +35,19 @@ XR_OK, XR_EINVAL, XR_EZERO_STATE, XR_ENOMEM, XR_ECUDA, XR_ETIMEOUT, XR_EUNSUPPOR
 _lib = None
 
 
+class ServerConfig(ctypes.Structure):
+    """xr_server_config of include/xr.h."""
+    _fields_ = [("arena_bytes", ctypes.c_uint64), ("nclients", ctypes.c_uint32),
+                ("max_rounds", ctypes.c_uint32), ("max_round_requests", ctypes.c_uint32),
+                ("mode", ctypes.c_int), ("outputs_per_row", ctypes.c_int), ("block", ctypes.c_int)]
+
+
+class ServeStats(ctypes.Structure):
+    """xr_serve_stats of include/xr.h."""
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "completed", "released", "rounds", "bytes",
+                                                "arena_in_use", "arena_peak")]
+
+
 class Request(ctypes.Structure):
     """xr_request of include/xr.h."""
     _fields_ = [("variant", ctypes.c_int), ("dtype", ctypes.c_int), ("n", ctypes.c_uint64),
@@ -98,6 +111,24 @@ def lib():
         L.xr_batch_get_config.restype = i
         L.xr_batch_tune.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]
         L.xr_batch_tune.restype = i
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.xr_server_create.argtypes = [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(i),
+                                       ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(vp)]
+        L.xr_server_destroy.argtypes = [vp]
+        L.xr_server_submit.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint64, i, ctypes.POINTER(ctypes.c_uint64)]
+        L.xr_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), dp]
+        L.xr_server_release.argtypes = [vp, ctypes.c_uint64]
+        L.xr_server_arena.argtypes = [vp]
+        L.xr_server_arena.restype = vp
+        L.xr_server_read.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, vp, vp]
+        L.xr_server_client_state.argtypes = [vp, ctypes.c_uint32, vp]
+        L.xr_server_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
+        L.xr_server_replay.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(i), sz, dp, dp]
+        for fn in ("xr_server_create", "xr_server_destroy", "xr_server_submit", "xr_server_wait",
+                   "xr_server_release", "xr_server_read", "xr_server_client_state", "xr_server_stats",
+                   "xr_server_replay"):
+            getattr(L, fn).restype = i
         for name, args in sigs.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -387,3 +418,90 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+SERVE_MODES = {"batched": 0, "plain": 1}
+
+
+class Server:
+    """Continuous batching for many clients with device-resident states
+    (xr_server_*).  client_variants / client_seeds: one entry per client."""
+
+    def __init__(self, ctx, client_variants, client_seeds, arena_bytes, mode="batched", max_rounds=3,
+                 max_round_requests=4096, outputs_per_row=0, block=0):
+        n = len(client_variants)
+        cfg = ServerConfig(arena_bytes, n, max_rounds, max_round_requests, SERVE_MODES[mode], outputs_per_row,
+                           block)
+        var = (ctypes.c_int * n)(*[_v(v) for v in client_variants])
+        seeds = (ctypes.c_uint64 * n)(*[int(x) & (2**64 - 1) for x in client_seeds])
+        h = ctypes.c_void_p()
+        _check(lib().xr_server_create(ctx.handle, ctypes.byref(cfg), var, seeds, ctypes.byref(h)),
+               "xr_server_create")
+        self._h = h
+        self.ctx = ctx
+        self.client_variants = list(client_variants)
+
+    def submit(self, client, n, dtype):
+        t = ctypes.c_uint64()
+        _check(lib().xr_server_submit(self._h, client, n, DTYPES[dtype], ctypes.byref(t)), "xr_server_submit")
+        return t.value
+
+    def wait(self, ticket):
+        off, lat = ctypes.c_uint64(), ctypes.c_double()
+        _check(lib().xr_server_wait(self._h, ticket, ctypes.byref(off), ctypes.byref(lat)), "xr_server_wait")
+        return off.value, lat.value
+
+    def release(self, ticket):
+        _check(lib().xr_server_release(self._h, ticket), "xr_server_release")
+
+    def read(self, offset, nbytes, dst, stream=None):
+        """Copy arena bytes into a tensor (host or device) of >= nbytes."""
+        if _nbytes(dst) < nbytes or not dst.is_contiguous():
+            raise ValueError("dst too small")
+        _check(lib().xr_server_read(self._h, offset, nbytes, dst.data_ptr(), _stream(stream)), "xr_server_read")
+
+    def client_state(self, client):
+        nb = state_bytes(self.client_variants[client])
+        buf = ctypes.create_string_buffer(32)
+        _check(lib().xr_server_client_state(self._h, client, buf), "xr_server_client_state")
+        return buf.raw[:nb]
+
+    def stats(self):
+        st = ServeStats()
+        _check(lib().xr_server_stats(self._h, ctypes.byref(st)), "xr_server_stats")
+        return {f: getattr(st, f) for f, _ in ServeStats._fields_}
+
+    def replay(self, arrival_us, clients, ns, dtypes):
+        """Submit request i at arrival_us[i] (us after the call starts), release
+        each output on completion; returns (latencies in us, wall time in us)."""
+        import numpy as np
+        n = len(ns)
+        arr = np.ascontiguousarray(arrival_us, dtype=np.float64)
+        cl = np.ascontiguousarray(clients, dtype=np.uint32)
+        nn = np.ascontiguousarray(ns, dtype=np.uint64)
+        dt = np.ascontiguousarray([DTYPES[d] if isinstance(d, str) else int(d) for d in dtypes], dtype=np.int32)
+        lat = np.zeros(n, dtype=np.float64)
+        wall = ctypes.c_double()
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(lib().xr_server_replay(self._h, arr.ctypes.data_as(dp), cl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                      nn.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                      dt.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n, lat.ctypes.data_as(dp),
+                                      ctypes.byref(wall)), "xr_server_replay")
+        return lat, wall.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().xr_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

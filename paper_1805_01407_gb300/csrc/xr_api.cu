@@ -160,6 +160,7 @@ static void pset_dists(int engine, int *d)
     d[0] = n / 2;
     d[1] = 3 * n / 4;
     d[2] = 10;
+    d[3] = 0;
 }
 
 namespace xr {

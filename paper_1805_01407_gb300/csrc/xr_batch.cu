@@ -18,6 +18,7 @@
 #include "xr_device.cuh"
 #include "xr_fill_impl.cuh"
 #include "xr_internal.h"
+#include "xr_batch_plan.h"
 
 namespace xr {
 
@@ -26,21 +27,6 @@ constexpr u64 BSEG = 1ull << BSEG_LOG2;
 constexpr int BATCH_NBUF = 2;            // staged rows per lane
 constexpr int SLOT_WORDS = 8;            // 32-byte state slots
 constexpr int TILE_BYTES_B = 32 * 128;   // one 32-row x 128-byte tile
-
-struct BReq {
-    u64 n, out_offset, slot, seg_base;
-    int variant, dtype;
-};
-
-struct BGroup {
-    int variant, dtype;
-    u32 nreq, req_first;
-    u64 nseg, prefix_first;
-};
-
-struct BLevelItem {
-    u64 parent, limit;  // parent segment index (absolute) and end of its request's segments
-};
 
 struct BatchDev {
     const BReq *reqs;
@@ -319,39 +305,10 @@ __global__ void __launch_bounds__(512)
 
 using namespace xr;
 
-// ---------------------------------------------------------------- host side
+// ---------------------------------------------------------------- host side: plans
 
-struct xr_batch {
-    xr_ctx *ctx;
-    size_t nreq;
-    u64 arena_bytes, ntasks, nseg_total;
-    // device plan
-    BReq *d_reqs;
-    BGroup *d_groups;
-    u32 *d_group_reqs;
-    u64 *d_prefix, *d_tasks;
-    unsigned long long *d_counter;
-    u32 *d_segstates;
-    BLevelItem *d_items;              // all level lists, concatenated
-    struct LevelLaunch {
-        int engine, level;
-        size_t first, count;
-    };
-    std::vector<LevelLaunch> levels;
-    // configuration
-    int opt, block;
-    // graph cache
-    cudaGraph_t graph;
-    cudaGraphExec_t exec;
-    const void *g_seeds, *g_slots, *g_out;
-    int g_opt, g_block;
-    cudaStream_t cap;
-    void *d_slot_backup;
-    size_t slot_backup_bytes;
-    size_t max_slot;
-};
+namespace xr {
 
-static int engine_of_variant(int v) { return v <= 2 ? 0 : (v == 4 ? 2 : (v <= 5 ? 1 : 3)); }
 static int es_of(int dtype) { return (dtype == XR_U64 || dtype == XR_F64) ? 8 : 4; }
 static bool dtype_ok_b(int v, int dt)
 {
@@ -361,11 +318,182 @@ static bool dtype_ok_b(int v, int dt)
     return false;
 }
 
-static int st_of(cudaError_t e)
+int check_requests(const xr_request *h, size_t nreq)
 {
-    if (e == cudaSuccess) return XR_OK;
-    if (e == cudaErrorMemoryAllocation) return XR_ENOMEM;
-    return XR_ECUDA;
+    std::vector<u64> slots;
+    slots.reserve(nreq);
+    for (size_t r = 0; r < nreq; ++r) {
+        const xr_request &q = h[r];
+        if (q.variant < 0 || q.variant >= XR_NUM_VARIANTS || !dtype_ok_b(q.variant, q.dtype)) return XR_EINVAL;
+        if (q.out_offset % 16) return XR_EINVAL;
+        if (q.n > (1ull << 50)) return XR_EINVAL;
+        slots.push_back(q.slot);
+    }
+    std::sort(slots.begin(), slots.end());
+    for (size_t i = 1; i < slots.size(); ++i)
+        if (slots[i] == slots[i - 1]) return XR_EINVAL;
+    return XR_OK;
+}
+
+// O(requests + tasks): tasks are 32-segment windows of each group; a window
+// lying inside the full segments of one row-aligned request is a full task.
+// Full tasks go first; the others follow by their longest lane, longest first.
+void build_plan(const xr_request *in, size_t nreq, HostPlan &p)
+{
+    p.reqs.resize(nreq);
+    p.groups.clear();
+    p.group_reqs.clear();
+    p.prefix.clear();
+    p.tasks.clear();
+    p.items.clear();
+    p.levels.clear();
+    u64 segs = 0, arena = 0, maxslot = 0;
+    for (size_t r = 0; r < nreq; ++r) {
+        BReq &q = p.reqs[r];
+        q.n = in[r].n;
+        q.out_offset = in[r].out_offset;
+        q.slot = in[r].slot;
+        q.seg_base = segs;
+        q.variant = in[r].variant;
+        q.dtype = in[r].dtype;
+        segs += (q.n + BSEG - 1) / BSEG;
+        arena = std::max<u64>(arena, q.out_offset + q.n * (u64)es_of(q.dtype));
+        maxslot = std::max<u64>(maxslot, q.slot);
+    }
+    p.nseg = segs;
+    p.arena_bytes = arena;
+    p.max_slot = maxslot;
+
+    std::vector<u32> bucket[XR_NUM_VARIANTS * 4];
+    for (size_t r = 0; r < nreq; ++r)
+        if (p.reqs[r].n) bucket[p.reqs[r].variant * 4 + p.reqs[r].dtype].push_back((u32)r);
+    std::vector<u64> partial[BSEG + 1];  // partial tasks by longest lane
+    for (int bi = 0; bi < XR_NUM_VARIANTS * 4; ++bi) {
+        if (bucket[bi].empty()) continue;
+        BGroup g;
+        g.variant = bi / 4;
+        g.dtype = bi % 4;
+        g.nreq = (u32)bucket[bi].size();
+        g.req_first = (u32)p.group_reqs.size();
+        g.prefix_first = p.prefix.size();
+        u64 acc = 0;
+        for (u32 r : bucket[bi]) {
+            p.group_reqs.push_back(r);
+            p.prefix.push_back(acc);
+            acc += (p.reqs[r].n + BSEG - 1) / BSEG;
+        }
+        p.prefix.push_back(acc);
+        g.nseg = acc;
+        const u64 gi = p.groups.size();
+        p.groups.push_back(g);
+        const u64 T = (acc + 31) / 32, rowbytes = BSEG * (u64)es_of(g.dtype);
+        std::vector<unsigned short> len(T, 0);
+        std::vector<char> full(T, 0);
+        u64 pre = 0;
+        for (u32 r : bucket[bi]) {
+            const BReq &q = p.reqs[r];
+            const u64 P = (q.n + BSEG - 1) / BSEG, fullseg = q.n / BSEG, last = q.n - (P - 1) * BSEG;
+            if (q.out_offset % rowbytes == 0) {
+                const u64 t0 = (pre + 31) / 32, t1 = (pre + fullseg) / 32;
+                for (u64 t = t0; t < t1; ++t) full[t] = 1;
+            }
+            for (u64 t = pre / 32; t <= (pre + P - 1) / 32; ++t) {
+                const u64 lo = std::max<u64>(pre, t * 32);
+                const u64 l = lo < pre + fullseg ? BSEG : last;
+                if (l > len[t]) len[t] = (unsigned short)l;
+            }
+            pre += P;
+        }
+        for (u64 t = 0; t < T; ++t) {
+            if (full[t]) p.tasks.push_back((gi << 40) | t | TASK_FULL);
+            else partial[len[t]].push_back((gi << 40) | t);
+        }
+    }
+    for (int l = (int)BSEG; l >= 0; --l)
+        p.tasks.insert(p.tasks.end(), partial[l].begin(), partial[l].end());
+
+    // levels of the segment-start scheme, per (level, engine)
+    for (int l = PSET_LEVELS - 1; l >= 0; --l) {
+        const u64 stride = 1ull << (PSET_BITS * l), span = stride << PSET_BITS;
+        for (int e = 0; e < NUM_ENGINES; ++e) {
+            LevelLaunch L;
+            L.engine = e;
+            L.level = l;
+            L.first = p.items.size();
+            for (size_t r = 0; r < nreq; ++r) {
+                if (engine_of(p.reqs[r].variant) != e) continue;
+                const u64 P = (p.reqs[r].n + BSEG - 1) / BSEG;
+                if (P <= stride) continue;
+                for (u64 k = 0; k * span < P; ++k)
+                    p.items.push_back({p.reqs[r].seg_base + k * span, p.reqs[r].seg_base + P});
+            }
+            L.count = p.items.size() - L.first;
+            if (L.count) p.levels.push_back(L);
+        }
+    }
+}
+
+void free_devplan(DevPlan &d)
+{
+    cudaFree(d.blob);
+    cudaFreeHost(d.pinned);
+    cudaFree(d.segstates);
+    cudaFree(d.counter);
+    d = DevPlan();
+}
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Copy the plan to the device: all arrays in one blob, one asynchronous copy
+// from pinned memory.  Buffers grow (after waiting for `st`) only when a plan
+// is larger than any before; the pinned blob is reused, so the caller must
+// not upload again before this copy has completed.
+cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st)
+{
+    d.off_reqs = 0;
+    d.off_groups = up256(d.off_reqs + p.reqs.size() * sizeof(BReq));
+    d.off_group_reqs = up256(d.off_groups + p.groups.size() * sizeof(BGroup));
+    d.off_prefix = up256(d.off_group_reqs + p.group_reqs.size() * sizeof(u32));
+    d.off_tasks = up256(d.off_prefix + p.prefix.size() * sizeof(u64));
+    d.off_items = up256(d.off_tasks + p.tasks.size() * sizeof(u64));
+    const size_t total = up256(d.off_items + p.items.size() * sizeof(BLevelItem)) + 256;
+    cudaError_t err = cudaSuccess;
+    if (total > d.blob_cap) {
+        err = cudaStreamSynchronize(st);
+        cudaFree(d.blob);
+        cudaFreeHost(d.pinned);
+        d.blob = d.pinned = nullptr;
+        d.blob_cap = 0;
+        const size_t cap = total + total / 2;
+        if (err == cudaSuccess) err = cudaMalloc((void **)&d.blob, cap);
+        if (err == cudaSuccess) err = cudaMallocHost((void **)&d.pinned, cap);
+        if (err != cudaSuccess) return err;
+        d.blob_cap = cap;
+    }
+    const size_t segbytes = (size_t)p.nseg * 32;
+    if (segbytes > d.seg_cap) {
+        err = cudaStreamSynchronize(st);
+        cudaFree(d.segstates);
+        d.segstates = nullptr;
+        d.seg_cap = 0;
+        if (err == cudaSuccess) err = cudaMalloc((void **)&d.segstates, segbytes);
+        if (err != cudaSuccess) return err;
+        d.seg_cap = segbytes;
+    }
+    if (!d.counter) {
+        err = cudaMalloc((void **)&d.counter, sizeof(unsigned long long));
+        if (err != cudaSuccess) return err;
+    }
+    auto put = [&](size_t off, const void *src, size_t bytes) {
+        if (bytes) memcpy(d.pinned + off, src, bytes);
+    };
+    put(d.off_reqs, p.reqs.data(), p.reqs.size() * sizeof(BReq));
+    put(d.off_groups, p.groups.data(), p.groups.size() * sizeof(BGroup));
+    put(d.off_group_reqs, p.group_reqs.data(), p.group_reqs.size() * sizeof(u32));
+    put(d.off_prefix, p.prefix.data(), p.prefix.size() * sizeof(u64));
+    put(d.off_tasks, p.tasks.data(), p.tasks.size() * sizeof(u64));
+    put(d.off_items, p.items.data(), p.items.size() * sizeof(BLevelItem));
+    return cudaMemcpyAsync(d.blob, d.pinned, total, cudaMemcpyHostToDevice, st);
 }
 
 static u32 bufstride_for(int opt) { return (u32)(opt * 8 + 16); }
@@ -377,232 +505,39 @@ static u32 warpbytes_for(int opt)
     const u32 w = rows > 2u * TILE_BYTES_B ? rows : 2u * TILE_BYTES_B;
     return (w + 1023u) & ~1023u;
 }
-static size_t smem_for(int opt, int block) { return (size_t)(block / 32) * warpbytes_for(opt) + 1024; }
+size_t batch_smem_bytes(int opt, int block) { return (size_t)(block / 32) * warpbytes_for(opt) + 1024; }
 
-extern "C" int xr_batch_destroy(xr_batch *b)
+// Enqueue one run of an uploaded plan on `st` (also under stream capture):
+// reset the task counter, seed or copy in segment 0 of every request, the
+// segment-start levels, then the persistent fill.  `rows_bytes` is the size
+// of the output allocation the row tensor maps may cover.
+cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint64_t *d_seeds, void *d_slots,
+                         void *d_out, u64 rows_bytes, int opt, int block, cudaStream_t st)
 {
-    if (!b) return XR_OK;
-    cudaSetDevice(b->ctx->device);
-    cudaDeviceSynchronize();
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    if (b->cap) cudaStreamDestroy(b->cap);
-    cudaFree(b->d_reqs);
-    cudaFree(b->d_groups);
-    cudaFree(b->d_group_reqs);
-    cudaFree(b->d_prefix);
-    cudaFree(b->d_tasks);
-    cudaFree(b->d_counter);
-    cudaFree(b->d_segstates);
-    cudaFree(b->d_items);
-    cudaFree(b->d_slot_backup);
-    delete b;
-    return XR_OK;
-}
-
-template <typename T>
-static cudaError_t upload(T **dst, const std::vector<T> &src)
-{
-    *dst = nullptr;
-    if (src.empty()) return cudaSuccess;
-    cudaError_t e = cudaMalloc((void **)dst, src.size() * sizeof(T));
-    if (e == cudaSuccess) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
-    return e;
-}
-
-extern "C" int xr_batch_create(xr_ctx *ctx, const xr_request *h_reqs, size_t nreq, xr_batch **out)
-{
-    if (!ctx || !out || (nreq && !h_reqs)) return XR_EINVAL;
-    *out = nullptr;
-    // checks
-    std::vector<u64> slots_seen;
-    slots_seen.reserve(nreq);
-    for (size_t r = 0; r < nreq; ++r) {
-        const xr_request &q = h_reqs[r];
-        if (q.variant < 0 || q.variant >= XR_NUM_VARIANTS || !dtype_ok_b(q.variant, q.dtype)) return XR_EINVAL;
-        if (q.out_offset % 16) return XR_EINVAL;
-        if (q.n > (1ull << 50)) return XR_EINVAL;
-        slots_seen.push_back(q.slot);
-    }
-    std::sort(slots_seen.begin(), slots_seen.end());
-    for (size_t i = 1; i < slots_seen.size(); ++i)
-        if (slots_seen[i] == slots_seen[i - 1]) return XR_EINVAL;
-
-    xr_batch *b = new xr_batch();  // value-initialized: every plain member starts at zero
-    b->ctx = ctx;
-    b->nreq = nreq;
-    b->opt = 16;
-    b->block = 256;
-    b->max_slot = slots_seen.empty() ? 0 : (size_t)slots_seen.back();
-
-    // requests and segment bases
-    std::vector<BReq> reqs(nreq);
-    u64 segs = 0, arena = 0;
-    for (size_t r = 0; r < nreq; ++r) {
-        const xr_request &q = h_reqs[r];
-        reqs[r].n = q.n;
-        reqs[r].out_offset = q.out_offset;
-        reqs[r].slot = q.slot;
-        reqs[r].seg_base = segs;
-        reqs[r].variant = q.variant;
-        reqs[r].dtype = q.dtype;
-        segs += (q.n + BSEG - 1) / BSEG;
-        arena = std::max<u64>(arena, q.out_offset + q.n * (u64)es_of(q.dtype));
-    }
-    b->nseg_total = segs;
-    b->arena_bytes = arena;
-
-    // groups by (variant, dtype)
-    std::vector<BGroup> groups;
-    std::vector<u32> group_reqs;
-    std::vector<u64> prefix;
-    struct TaskKey {
-        u64 code;
-        u64 len;  // longest lane of the task
-    };
-    std::vector<TaskKey> tasks;
-    for (int v = 0; v < XR_NUM_VARIANTS; ++v)
-        for (int dt = 0; dt < 4; ++dt) {
-            std::vector<u32> members;
-            for (size_t r = 0; r < nreq; ++r)
-                if (reqs[r].variant == v && reqs[r].dtype == dt && reqs[r].n > 0) members.push_back((u32)r);
-            if (members.empty()) continue;
-            BGroup g;
-            g.variant = v;
-            g.dtype = dt;
-            g.nreq = (u32)members.size();
-            g.req_first = (u32)group_reqs.size();
-            g.prefix_first = prefix.size();
-            u64 acc = 0;
-            std::vector<u64> seglen;  // length of every segment of the group, in order
-            std::vector<u32> segreq;  // its request
-            for (u32 r : members) {
-                group_reqs.push_back(r);
-                prefix.push_back(acc);
-                const u64 P = (reqs[r].n + BSEG - 1) / BSEG;
-                for (u64 q = 0; q < P; ++q) {
-                    seglen.push_back(std::min<u64>(BSEG, reqs[r].n - q * BSEG));
-                    segreq.push_back(r);
-                }
-                acc += P;
-            }
-            const u64 rowbytes = BSEG * (u64)es_of(dt);
-            prefix.push_back(acc);
-            g.nseg = acc;
-            const u64 gi = groups.size();
-            groups.push_back(g);
-            for (u64 t = 0; t * 32 < acc; ++t) {
-                u64 len = 0;
-                const u64 s0 = t * 32, s1 = std::min<u64>(acc, t * 32 + 32);
-                bool full = (s1 - s0 == 32) && reqs[segreq[s0]].out_offset % rowbytes == 0;
-                for (u64 s = s0; s < s1; ++s) {
-                    len = std::max(len, seglen[s]);
-                    full = full && seglen[s] == BSEG && segreq[s] == segreq[s0];
-                }
-                tasks.push_back({(gi << 40) | t | (full ? TASK_FULL : 0ull), len});
-            }
-        }
-    // longest tasks first: short ones fill the tail of the persistent grid
-    std::stable_sort(tasks.begin(), tasks.end(), [](const TaskKey &a, const TaskKey &c) { return a.len > c.len; });
-    std::vector<u64> task_codes(tasks.size());
-    for (size_t i = 0; i < tasks.size(); ++i) task_codes[i] = tasks[i].code;
-    b->ntasks = task_codes.size();
-
-    // level lists per (engine, level) of the segment-start scheme
-    std::vector<BLevelItem> items;
-    for (int l = PSET_LEVELS - 1; l >= 0; --l) {
-        const u64 stride = 1ull << (PSET_BITS * l), span = stride << PSET_BITS;
-        for (int e = 0; e < NUM_ENGINES; ++e) {
-            xr_batch::LevelLaunch L;
-            L.engine = e;
-            L.level = l;
-            L.first = items.size();
-            for (size_t r = 0; r < nreq; ++r) {
-                if (engine_of_variant(reqs[r].variant) != e) continue;
-                const u64 P = (reqs[r].n + BSEG - 1) / BSEG;
-                if (P <= stride) continue;
-                for (u64 p = 0; p * span < P; ++p) items.push_back({reqs[r].seg_base + p * span, reqs[r].seg_base + P});
-            }
-            L.count = items.size() - L.first;
-            if (L.count) b->levels.push_back(L);
-        }
-    }
-
-    cudaError_t err = cudaSetDevice(ctx->device);
-    if (err == cudaSuccess) err = upload(&b->d_reqs, reqs);
-    if (err == cudaSuccess) err = upload(&b->d_groups, groups);
-    if (err == cudaSuccess) err = upload(&b->d_group_reqs, group_reqs);
-    if (err == cudaSuccess) err = upload(&b->d_prefix, prefix);
-    if (err == cudaSuccess) err = upload(&b->d_tasks, task_codes);
-    if (err == cudaSuccess) err = upload(&b->d_items, items);
-    if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_counter, sizeof(unsigned long long));
-    if (err == cudaSuccess && segs) err = cudaMalloc((void **)&b->d_segstates, segs * 32);
-    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-    if (err == cudaSuccess) {
-        static bool attr = false;
-        if (!attr) {
-            err = cudaFuncSetAttribute(k_batch_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-            attr = (err == cudaSuccess);
-        }
-    }
-    if (err != cudaSuccess) {
-        xr_batch_destroy(b);
-        return st_of(err);
-    }
-    *out = b;
-    return XR_OK;
-}
-
-extern "C" uint64_t xr_batch_arena_bytes(const xr_batch *b) { return b ? b->arena_bytes : 0; }
-extern "C" uint64_t xr_batch_tasks(const xr_batch *b) { return b ? b->ntasks : 0; }
-
-extern "C" int xr_batch_set_config(xr_batch *b, int opt, int block)
-{
-    if (!b) return XR_EINVAL;
-    if (opt != 4 && opt != 8 && opt != 16 && opt != 32 && opt != 64) return XR_EINVAL;
-    if (block != 128 && block != 256 && block != 512) return XR_EINVAL;
-    if (smem_for(opt, block) > 227 * 1024) return XR_EINVAL;
-    b->opt = opt;
-    b->block = block;
-    return XR_OK;
-}
-
-extern "C" int xr_batch_get_config(const xr_batch *b, int *opt, int *block)
-{
-    if (!b || !opt || !block) return XR_EINVAL;
-    *opt = b->opt;
-    *block = b->block;
-    return XR_OK;
-}
-
-// Enqueue one run on `st` (not captured, or being captured).
-static cudaError_t enqueue_run(xr_batch *b, const uint64_t *d_seeds, void *d_slots, void *d_out, cudaStream_t st)
-{
-    xr_ctx *ctx = b->ctx;
     BatchDev d;
-    d.reqs = b->d_reqs;
-    d.groups = b->d_groups;
-    d.group_reqs = b->d_group_reqs;
-    d.prefix = b->d_prefix;
-    d.tasks = b->d_tasks;
-    d.ntasks = b->ntasks;
-    d.counter = b->d_counter;
-    d.segstates = b->d_segstates;
+    d.reqs = (const BReq *)(dp.blob + dp.off_reqs);
+    d.groups = (const BGroup *)(dp.blob + dp.off_groups);
+    d.group_reqs = (const u32 *)(dp.blob + dp.off_group_reqs);
+    d.prefix = (const u64 *)(dp.blob + dp.off_prefix);
+    d.tasks = (const u64 *)(dp.blob + dp.off_tasks);
+    const BLevelItem *items = (const BLevelItem *)(dp.blob + dp.off_items);
+    d.ntasks = p.tasks.size();
+    d.counter = dp.counter;
+    d.segstates = dp.segstates;
     d.slots = (unsigned char *)d_slots;
     d.out = (unsigned char *)d_out;
     d.seeds = reinterpret_cast<const u64 *>(d_seeds);
     d.status = ctx->d_status;
-    d.opt = b->opt;
-    d.bufstride = bufstride_for(b->opt);
-    d.warpbytes = warpbytes_for(b->opt);
-    // tensor maps over the arena as rows of 1024 elements (8- and 4-byte)
+    d.opt = opt;
+    d.bufstride = bufstride_for(opt);
+    d.warpbytes = warpbytes_for(opt);
     CUtensorMap maps[2];
     memset(maps, 0, sizeof(maps));
     d.rows_ok = 0;
     if (ctx->encode && d_out && ((uintptr_t)d_out % 16) == 0) {
         d.rows_ok = 1;
         for (int k = 0; k < 2; ++k) {
-            const u64 es = k == 0 ? 8 : 4, rows = b->arena_bytes / (BSEG * es);
+            const u64 es = k == 0 ? 8 : 4, rows = rows_bytes / (BSEG * es);
             if (rows == 0) continue;
             if (rows >= (1ull << 31)) {
                 d.rows_ok = 0;
@@ -619,13 +554,14 @@ static cudaError_t enqueue_run(xr_batch *b, const uint64_t *d_seeds, void *d_slo
                 d.rows_ok = 0;
         }
     }
-    cudaError_t err = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st);
-    if (err != cudaSuccess || b->nreq == 0) return err;
-    k_batch_seed<<<(unsigned)((b->nreq + 127) / 128), 128, 0, st>>>(d, b->nreq);
+    const size_t nreq = p.reqs.size();
+    cudaError_t err = cudaMemsetAsync(dp.counter, 0, sizeof(unsigned long long), st);
+    if (err != cudaSuccess || nreq == 0) return err;
+    k_batch_seed<<<(unsigned)((nreq + 127) / 128), 128, 0, st>>>(d, nreq);
     count_launch();
     err = cudaGetLastError();
-    for (size_t i = 0; i < b->levels.size() && err == cudaSuccess; ++i) {
-        const xr_batch::LevelLaunch &L = b->levels[i];
+    for (size_t i = 0; i < p.levels.size() && err == cudaSuccess; ++i) {
+        const LevelLaunch &L = p.levels[i];
         const int di = pset_index(L.engine, BSEG_LOG2);
         const int n = engine_bits(L.engine);
         const size_t set_words = (size_t)PSET_SIZE * n * (n / 32);
@@ -633,36 +569,130 @@ static cudaError_t enqueue_run(xr_batch *b, const uint64_t *d_seeds, void *d_slo
         const dim3 grid((unsigned)((L.count + 255) / 256), PSET_SIZE - 1);
         const u64 stride = 1ull << (PSET_BITS * L.level);
         if (n == 256)
-            k_batch_level<8><<<grid, 256, 0, st>>>(P, b->d_items + L.first, L.count, stride, b->d_segstates);
+            k_batch_level<8><<<grid, 256, 0, st>>>(P, items + L.first, L.count, stride, dp.segstates);
         else
-            k_batch_level<4><<<grid, 256, 0, st>>>(P, b->d_items + L.first, L.count, stride, b->d_segstates);
+            k_batch_level<4><<<grid, 256, 0, st>>>(P, items + L.first, L.count, stride, dp.segstates);
         count_launch();
         err = cudaGetLastError();
     }
-    if (err != cudaSuccess || b->ntasks == 0) return err;
+    if (err != cudaSuccess || p.tasks.empty()) return err;
+    static bool attr = false;
+    if (!attr) {
+        err = cudaFuncSetAttribute(k_batch_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (err != cudaSuccess) return err;
+        attr = true;
+    }
     int per_sm = 0, sms = 0;
-    const size_t smem = smem_for(b->opt, b->block);
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_fill, b->block, smem);
+    const size_t smem = batch_smem_bytes(opt, block);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_fill, block, smem);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    u64 grid = (u64)per_sm * sms;
-    const u64 warps_needed = b->ntasks, warps_per_block = (u64)b->block / 32;
-    grid = std::min<u64>(grid, (warps_needed + warps_per_block - 1) / warps_per_block);
-    k_batch_fill<<<(unsigned)grid, b->block, smem, st>>>(d, maps[0], maps[1]);
+    const u64 warps_per_block = (u64)block / 32;
+    const u64 grid = std::min<u64>((u64)per_sm * sms, (p.tasks.size() + warps_per_block - 1) / warps_per_block);
+    k_batch_fill<<<(unsigned)grid, block, smem, st>>>(d, maps[0], maps[1]);
     count_launch();
     return cudaGetLastError();
+}
+
+}  // namespace xr
+
+using namespace xr;
+
+// ---------------------------------------------------------------- the public batch
+
+struct xr_batch {
+    xr_ctx *ctx = nullptr;
+    HostPlan plan;
+    DevPlan dev;
+    int opt = 16, block = 128;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void *g_seeds = nullptr, *g_slots = nullptr, *g_out = nullptr;
+    int g_opt = 0, g_block = 0;
+    cudaStream_t cap = nullptr;
+    void *d_slot_backup = nullptr;
+    size_t slot_backup_bytes = 0;
+};
+
+static int st_of(cudaError_t e)
+{
+    if (e == cudaSuccess) return XR_OK;
+    if (e == cudaErrorMemoryAllocation) return XR_ENOMEM;
+    return XR_ECUDA;
+}
+
+extern "C" int xr_batch_destroy(xr_batch *b)
+{
+    if (!b) return XR_OK;
+    cudaSetDevice(b->ctx->device);
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    free_devplan(b->dev);
+    cudaFree(b->d_slot_backup);
+    delete b;
+    return XR_OK;
+}
+
+extern "C" int xr_batch_create(xr_ctx *ctx, const xr_request *h_reqs, size_t nreq, xr_batch **out)
+{
+    if (!ctx || !out || (nreq && !h_reqs)) return XR_EINVAL;
+    *out = nullptr;
+    const int rc = check_requests(h_reqs, nreq);
+    if (rc != XR_OK) return rc;
+    xr_batch *b = new xr_batch();
+    b->ctx = ctx;
+    build_plan(h_reqs, nreq, b->plan);
+    cudaError_t err = cudaSetDevice(ctx->device);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = upload_plan(b->plan, b->dev, b->cap);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(b->cap);
+    if (err != cudaSuccess) {
+        xr_batch_destroy(b);
+        return st_of(err);
+    }
+    *out = b;
+    return XR_OK;
+}
+
+extern "C" uint64_t xr_batch_arena_bytes(const xr_batch *b) { return b ? b->plan.arena_bytes : 0; }
+extern "C" uint64_t xr_batch_tasks(const xr_batch *b) { return b ? (uint64_t)b->plan.tasks.size() : 0; }
+
+extern "C" int xr_batch_set_config(xr_batch *b, int opt, int block)
+{
+    if (!b) return XR_EINVAL;
+    if (opt != 4 && opt != 8 && opt != 16 && opt != 32 && opt != 64) return XR_EINVAL;
+    if (block != 128 && block != 256 && block != 512) return XR_EINVAL;
+    if (batch_smem_bytes(opt, block) > 227 * 1024) return XR_EINVAL;
+    b->opt = opt;
+    b->block = block;
+    return XR_OK;
+}
+
+extern "C" int xr_batch_get_config(const xr_batch *b, int *opt, int *block)
+{
+    if (!b || !opt || !block) return XR_EINVAL;
+    *opt = b->opt;
+    *block = b->block;
+    return XR_OK;
+}
+
+static cudaError_t batch_enqueue(xr_batch *b, const uint64_t *d_seeds, void *d_slots, void *d_out, cudaStream_t st)
+{
+    return enqueue_plan(b->ctx, b->plan, b->dev, d_seeds, d_slots, d_out, b->plan.arena_bytes, b->opt, b->block, st);
 }
 
 extern "C" int xr_batch_run(xr_batch *b, const uint64_t *d_seeds, void *d_slots, void *d_out, int use_graph,
                             void *stream)
 {
     if (!b) return XR_EINVAL;
-    if (b->nreq == 0) return XR_OK;
+    if (b->plan.reqs.empty()) return XR_OK;
     if (!d_slots || ((uintptr_t)d_slots % 16)) return XR_EINVAL;
-    if (b->arena_bytes && (!d_out || ((uintptr_t)d_out % 16))) return XR_EINVAL;
+    if (b->plan.arena_bytes && (!d_out || ((uintptr_t)d_out % 16))) return XR_EINVAL;
     const cudaStream_t st = (cudaStream_t)stream;
-    if (!use_graph) return st_of(enqueue_run(b, d_seeds, d_slots, d_out, st));
+    if (!use_graph) return st_of(batch_enqueue(b, d_seeds, d_slots, d_out, st));
     if (!b->exec || b->g_seeds != d_seeds || b->g_slots != d_slots || b->g_out != d_out || b->g_opt != b->opt ||
         b->g_block != b->block) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -671,7 +701,7 @@ extern "C" int xr_batch_run(xr_batch *b, const uint64_t *d_seeds, void *d_slots,
         b->graph = nullptr;
         cudaError_t err = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (err != cudaSuccess) return st_of(err);
-        cudaError_t e1 = enqueue_run(b, d_seeds, d_slots, d_out, b->cap);
+        cudaError_t e1 = batch_enqueue(b, d_seeds, d_slots, d_out, b->cap);
         err = cudaStreamEndCapture(b->cap, &b->graph);
         if (e1 != cudaSuccess) return st_of(e1);
         if (err != cudaSuccess) return st_of(err);
@@ -691,7 +721,7 @@ extern "C" int xr_batch_tune(xr_batch *b, const uint64_t *d_seeds, void *d_slots
 {
     if (!b || !d_slots) return XR_EINVAL;
     const cudaStream_t st = (cudaStream_t)stream;
-    const size_t nbytes = (b->max_slot + 1) * 32;
+    const size_t nbytes = (size_t)(b->plan.max_slot + 1) * 32;
     cudaError_t err = cudaSuccess;
     if (b->slot_backup_bytes < nbytes) {
         cudaFree(b->d_slot_backup);
@@ -709,19 +739,19 @@ extern "C" int xr_batch_tune(xr_batch *b, const uint64_t *d_seeds, void *d_slots
     int bo = b->opt, bb = b->block;
     for (int oi = 0; oi < 5 && err == cudaSuccess; ++oi)
         for (int bi = 0; bi < 3 && err == cudaSuccess; ++bi) {
-            if (smem_for(opts[oi], blocks[bi]) > 227 * 1024) continue;
+            if (batch_smem_bytes(opts[oi], blocks[bi]) > 227 * 1024) continue;
             b->opt = opts[oi];
             b->block = blocks[bi];
             float ms = 1e30f;
             for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
                 err = cudaMemcpyAsync(d_slots, b->d_slot_backup, nbytes, cudaMemcpyDeviceToDevice, st);
                 if (err == cudaSuccess) err = cudaEventRecord(e0, st);
-                if (err == cudaSuccess) err = enqueue_run(b, d_seeds, d_slots, d_out, st);
+                if (err == cudaSuccess) err = batch_enqueue(b, d_seeds, d_slots, d_out, st);
                 if (err == cudaSuccess) err = cudaEventRecord(e1, st);
                 if (err == cudaSuccess) err = cudaEventSynchronize(e1);
                 float t = 0;
                 if (err == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
-                if (rep > 0) ms = std::min(ms, t);  // first repetition warms up
+                if (rep > 0) ms = std::min(ms, t);  // the first repetition warms up
             }
             if (err == cudaSuccess && ms < best) {
                 best = ms;

@@ -1,0 +1,65 @@
+// xr_batch_plan.h -- host plans of batched requests (shared by the batch API
+// and the server): the request table, the (generator, dtype) groups, the warp
+// tasks and the segment-start level lists, and their device copies.
+#pragma once
+
+#include <vector>
+
+#include "xr_internal.h"
+
+namespace xr {
+
+typedef unsigned long long u64_t;
+
+struct BReq {
+    u64_t n, out_offset, slot, seg_base;
+    int variant, dtype;
+};
+
+struct BGroup {
+    int variant, dtype;
+    unsigned int nreq, req_first;
+    u64_t nseg, prefix_first;
+};
+
+struct BLevelItem {
+    u64_t parent, limit;  // parent segment index (absolute) and end of its request's segments
+};
+
+struct LevelLaunch {
+    int engine, level;
+    size_t first, count;
+};
+
+struct HostPlan {
+    std::vector<BReq> reqs;
+    std::vector<BGroup> groups;
+    std::vector<unsigned int> group_reqs;
+    std::vector<u64_t> prefix;
+    std::vector<u64_t> tasks;
+    std::vector<BLevelItem> items;
+    std::vector<LevelLaunch> levels;
+    u64_t nseg = 0, arena_bytes = 0, max_slot = 0;
+};
+
+// Device copy of a plan: one blob (arrays at 256-byte aligned offsets), the
+// segment-state scratch and the task counter; a pinned host blob of the same
+// layout feeds one asynchronous copy per upload.
+struct DevPlan {
+    unsigned char *blob = nullptr, *pinned = nullptr;
+    size_t blob_cap = 0;
+    unsigned int *segstates = nullptr;
+    size_t seg_cap = 0;
+    unsigned long long *counter = nullptr;
+    size_t off_reqs = 0, off_groups = 0, off_group_reqs = 0, off_prefix = 0, off_tasks = 0, off_items = 0;
+};
+
+int check_requests(const xr_request *h, size_t nreq);
+void build_plan(const xr_request *in, size_t nreq, HostPlan &p);
+cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st);
+void free_devplan(DevPlan &d);
+size_t batch_smem_bytes(int opt, int block);
+cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint64_t *d_seeds, void *d_slots,
+                         void *d_out, u64_t rows_bytes, int opt, int block, cudaStream_t st);
+
+}  // namespace xr

@@ -68,8 +68,9 @@ cudaError_t launch_seed(int variant, const uint64_t *d_seeds, uint64_t seed, siz
 
 }  // namespace xr
 
-// Jump distances with power sets, per engine: jump, long jump, xr_fill_seq segment.
-static const int NUM_PSET_DISTS = 3;
+// Jump distances with power sets, per engine: jump, long jump, xr_fill_seq
+// segment (2^10), and single steps (2^0, used to advance by any n).
+static const int NUM_PSET_DISTS = 4;
 
 // The context (opaque in include/xr.h).
 struct xr_ctx {

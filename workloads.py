@@ -83,3 +83,27 @@ def batch_requests(nreq=4096, max_len=1 << 24, mix_seed=4, variants=BULK_VARIANT
         name = variants[int(v[r])]
         out.append((name, native_dtype(name) if dt[r] == 0 else "f64", int(n[r]), r))
     return out
+
+
+# Serving: 256 clients (half xoshiro256**, half xoroshiro128++) with
+# device-resident states seeded by SplitMix64(client), Poisson arrivals at
+# 20k requests/s, sizes log-uniform in [2^10, 2^26] values, output type
+# uniform over {uint64, double}, a 16 GiB output budget.
+CONFIG_SERVE = dict(nclients=256, rate=20000.0, min_len=1 << 10, max_len=1 << 26, arena_bytes=16 << 30,
+                    trace_seed=6)
+
+
+def serve_clients(nclients=256):
+    return [("xoshiro256**" if c % 2 == 0 else "xoroshiro128++") for c in range(nclients)], list(range(nclients))
+
+
+def serve_trace(nreq, nclients=256, rate=20000.0, min_len=1 << 10, max_len=1 << 26, trace_seed=6, **_):
+    """(arrival_us, client, n, dtype) arrays for nreq Poisson arrivals."""
+    rng = np.random.default_rng(trace_seed)
+    gaps = rng.exponential(1e6 / rate, size=nreq) if rate > 0 else np.zeros(nreq)
+    arrival = np.cumsum(gaps) - gaps[0]
+    client = rng.integers(0, nclients, size=nreq).astype(np.uint32)
+    n = np.floor(np.exp(rng.uniform(np.log(min_len), np.log(max_len + 1.0), size=nreq))).astype(np.uint64)
+    n = np.clip(n, min_len, max_len)
+    dtype = np.where(rng.integers(0, 2, size=nreq) == 0, "u64", "f64")
+    return arrival, client, n, list(dtype)
