@@ -49,6 +49,7 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-extra", action="store_true")
     p.add_argument("--serve-requests", type=int, default=20000)
     p.add_argument("--batched-steps", type=int, default=5)
     p.add_argument("--profile", choices=["fill", "streams", "batch"], default=None,
@@ -400,6 +401,8 @@ def run_xr(args):
         line["batched"] = run_batched(xr, ctx, args)
     if not args.no_serve:
         line["serving"] = run_serving(xr, ctx, args)
+    if not args.no_extra:
+        line["extra_generators"] = run_extra(xr, ctx, args)
     if not args.no_e2e:
         line["e2e"] = run_e2e(ctx, args, first, bytes_per_step, world, dist)
     if dist:
@@ -472,6 +475,38 @@ def run_batched(xr, ctx, args):
         "tuned": {"outputs_per_row": opt, "block": block, "best_trial_ms": tune_ms},
         "tasks": b.tasks if False else None,
     }
+
+
+def run_extra(xr, ctx, args):
+    """The other generators of the paper at the bulk size (2^20 streams x 2^10
+    outputs, SplitMix64(42) base, jump-started): fill GB/s per output type,
+    median of 5 launches timed with events on their stream."""
+    import torch
+    S, m, seed = W.CONFIG_BULK["S"], W.CONFIG_BULK["m"], W.CONFIG_BULK["seed"]
+    stream = torch.cuda.current_stream()
+    res = {}
+    for v in W.EXTRA_VARIANTS:
+        base = ctx.empty_states(v, 1)
+        states = ctx.empty_states(v, S)
+        ctx.seed(v, seed, base)
+        ctx.make_streams(v, "jump", base, 0, S, states)
+        for d in (W.native_dtype(v), "f64"):
+            out = ctx.empty_output(S * m, d)
+            ctx.fill(v, states, S, m, d, out)
+            ts = []
+            for _ in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.fill(v, states, S, m, d, out)
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = statistics.median(ts)
+            res["%s/%s" % (v, d)] = {"fill_gbs": S * m * dtype_bytes(d) / (ms / 1e3) / 1e9, "fill_ms": ms}
+            del out
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    return res
 
 
 def run_serving(xr, ctx, args):

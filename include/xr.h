@@ -27,8 +27,13 @@
  *     without waiting, unless its comment says otherwise.
  *   - A state is stored as its words in order, little-endian: 4 x uint64 (32 B)
  *     for xoshiro256, 2 x uint64 (16 B) for xoroshiro128, 4 x uint32 (16 B) for
- *     xoshiro128.  Arrays of states are contiguous, state i at byte i * state
- *     bytes.  A state must not be all zero (captions of Figs. 1 and 3).
+ *     xoshiro128, 2 x uint32 (8 B) for xoroshiro64, 8 x uint64 (64 B) for
+ *     xoshiro512, 16 x uint64 (128 B, the word that the paper's cyclic index p
+ *     points past first) for xoroshiro1024.  Arrays of states are contiguous,
+ *     state i at byte i * state bytes.  A state must not be all zero (captions
+ *     of Figs. 1 to 4).
+ *   - The jump tables of the 512- and 1024-bit engines (16 and 128 MiB) are
+ *     built on the first call that needs them (a one-off wait of some ms).
  *   - Every call returns an xr status code.  Host-side argument errors return
  *     XR_EINVAL before any work is enqueued.  A failed CUDA launch or copy
  *     returns XR_ECUDA.  Errors found by kernels (an all-zero state) are
@@ -69,7 +74,17 @@ enum xr_variant {
     XR_XOSHIRO128_PLUSPLUS = 6,   /* 32-bit: rotl(s0 + s3, 7) + s0 */
     XR_XOSHIRO128_STARSTAR = 7,   /* 32-bit: rotl(s1 * 5, 7) * 9 */
     XR_XOSHIRO128_PLUS = 8,       /* 32-bit: s0 + s3 */
-    XR_NUM_VARIANTS = 9
+    /* further generators of Sec. 5 (Tables 4, 5, 7, 8; Figs. 1, 2, 4) */
+    XR_XOROSHIRO128_STAR = 9,     /* s0 * 0x9e3779b97f4a7c13, engine (24,16,37) */
+    XR_XOROSHIRO64_STAR = 10,     /* 32-bit, engine (26,9,13): s0 * 0x9E3779BB */
+    XR_XOROSHIRO64_STARSTAR = 11, /* 32-bit: rotl(s0 * 0x9E3779BB, 5) * 5 */
+    XR_XOSHIRO512_PLUS = 12,      /* engine S_8w (11,21): s0 + s2 */
+    XR_XOSHIRO512_PLUSPLUS = 13,  /* rotl(s0 + s2, 17) + s2 */
+    XR_XOSHIRO512_STARSTAR = 14,  /* rotl(s1 * 5, 7) * 9 */
+    XR_XOROSHIRO1024_STAR = 15,   /* engine X_kw, k = 16 (25,27,36): s0 * 0x9e3779b97f4a7c13 */
+    XR_XOROSHIRO1024_PLUSPLUS = 16, /* rotl(s0 + s15, 23) + s15 */
+    XR_XOROSHIRO1024_STARSTAR = 17, /* rotl(s0 * 5, 7) * 9 */
+    XR_NUM_VARIANTS = 18
 };
 
 /* Value type of the outputs. */
@@ -107,10 +122,10 @@ int xr_ctx_create(int device, xr_ctx **out);
 int xr_ctx_destroy(xr_ctx *ctx);
 
 /* ---- properties (pure host functions, no GPU needed) -------------------- */
-int xr_state_words(int variant);      /* 4, 2 or 4; -1 for a bad variant */
+int xr_state_words(int variant);      /* 2 .. 16; -1 for a bad variant */
 int xr_word_bits(int variant);        /* 64 or 32; -1 for a bad variant */
-int xr_state_bytes(int variant);      /* 32 or 16; -1 for a bad variant */
-int xr_state_bits(int variant);       /* n = 256 or 128; -1 for a bad variant */
+int xr_state_bytes(int variant);      /* 8 .. 128; -1 for a bad variant */
+int xr_state_bits(int variant);       /* n = 64 .. 1024; -1 for a bad variant */
 int xr_dtype_bytes(int dtype);        /* 8, 4, 8, 4; -1 for a bad dtype */
 const char *xr_variant_name(int variant);  /* e.g. "xoshiro256**"; NULL if bad */
 const char *xr_error_string(int status);   /* never NULL */

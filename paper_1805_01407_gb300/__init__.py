@@ -7,8 +7,9 @@ buffer is large enough for the call, and turns status codes into exceptions.
 There is no CPU fallback: if libxr.so is missing the import of the native
 library fails loudly.
 
-Generators (Blackman & Vigna, arXiv 1805.01407): xoshiro256+/++/** and
-xoroshiro128+/++/** (64-bit words), xoshiro128++/**/+ (32-bit words).
+Generators (Blackman & Vigna, arXiv 1805.01407): xoshiro256+/++/**,
+xoroshiro128+/++/**/*, xoshiro512+/++/**, xoroshiro1024*/++/** (64-bit words),
+xoshiro128++/**/+ and xoroshiro64*/** (32-bit words).
 """
 from __future__ import annotations
 
@@ -25,6 +26,9 @@ VARIANTS = {
     "xoshiro256+": 0, "xoshiro256++": 1, "xoshiro256**": 2,
     "xoroshiro128+": 3, "xoroshiro128++": 4, "xoroshiro128**": 5,
     "xoshiro128++": 6, "xoshiro128**": 7, "xoshiro128+": 8,
+    "xoroshiro128*": 9, "xoroshiro64*": 10, "xoroshiro64**": 11,
+    "xoshiro512+": 12, "xoshiro512++": 13, "xoshiro512**": 14,
+    "xoroshiro1024*": 15, "xoroshiro1024++": 16, "xoroshiro1024**": 17,
 }
 DTYPES = {"u64": 0, "u32": 1, "f64": 2, "f32": 3}
 LAYOUTS = {"stream": 0, "interleaved": 1}

@@ -2,6 +2,7 @@
 // the context (jump tables, status word, scratch), and dispatch to kernels.
 #include <stdlib.h>
 #include <atomic>
+#include <mutex>
 #include <string.h>
 
 #include "xr_device.cuh"
@@ -22,11 +23,19 @@ extern template cudaError_t launch_fill_v<5>(int, int, void *, size_t, size_t, s
 extern template cudaError_t launch_fill_v<6>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
 extern template cudaError_t launch_fill_v<7>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
 extern template cudaError_t launch_fill_v<8>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
+#define XR_EXTERN_FILL(V) \
+    extern template cudaError_t launch_fill_v<V>(int, int, void *, size_t, size_t, size_t, void *, int, int *, cudaStream_t, EncodeTiledFn);
+XR_EXTERN_FILL(9) XR_EXTERN_FILL(10) XR_EXTERN_FILL(11) XR_EXTERN_FILL(12) XR_EXTERN_FILL(13)
+XR_EXTERN_FILL(14) XR_EXTERN_FILL(15) XR_EXTERN_FILL(16) XR_EXTERN_FILL(17)
+#undef XR_EXTERN_FILL
 
-static const int kEngineOf[XR_NUM_VARIANTS] = {ENG_XOSHIRO256, ENG_XOSHIRO256, ENG_XOSHIRO256,
-                                               ENG_XOROSHIRO128, ENG_XOROSHIRO128PP, ENG_XOROSHIRO128,
-                                               ENG_XOSHIRO128, ENG_XOSHIRO128, ENG_XOSHIRO128};
-static const int kEngineBits[NUM_ENGINES] = {256, 128, 128, 128};
+static const int kEngineOf[XR_NUM_VARIANTS] = {
+    ENG_XOSHIRO256, ENG_XOSHIRO256, ENG_XOSHIRO256, ENG_XOROSHIRO128, ENG_XOROSHIRO128PP, ENG_XOROSHIRO128,
+    ENG_XOSHIRO128, ENG_XOSHIRO128, ENG_XOSHIRO128, ENG_XOROSHIRO128, ENG_XOROSHIRO64, ENG_XOROSHIRO64,
+    ENG_XOSHIRO512, ENG_XOSHIRO512, ENG_XOSHIRO512, ENG_XOROSHIRO1024, ENG_XOROSHIRO1024, ENG_XOROSHIRO1024};
+static const int kEngineBits[NUM_ENGINES] = {256, 128, 128, 128, 64, 512, 1024};
+static const int kEngineWords[NUM_ENGINES] = {4, 2, 2, 4, 2, 8, 16};
+static const int kEngineWordBits[NUM_ENGINES] = {64, 64, 64, 32, 32, 64, 64};
 static_assert(NUM_ENGINES == NUM_ENGINES_H, "engine count");
 
 static std::atomic<uint64_t> g_launches{0};
@@ -49,6 +58,15 @@ cudaError_t launch_fill(int variant, int dtype, int layout, void *states, size_t
     case 6: return launch_fill_v<6>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
     case 7: return launch_fill_v<7>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
     case 8: return launch_fill_v<8>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 9: return launch_fill_v<9>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 10: return launch_fill_v<10>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 11: return launch_fill_v<11>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 12: return launch_fill_v<12>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 13: return launch_fill_v<13>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 14: return launch_fill_v<14>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 15: return launch_fill_v<15>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 16: return launch_fill_v<16>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
+    case 17: return launch_fill_v<17>(dtype, layout, states, S, m, ld, out, write_back, status, stream, encode);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -65,8 +83,9 @@ static const int SEQ_LOG2 = 10;
 static const size_t HOST_STAGING_BYTES = (size_t)256 << 20;
 
 static const char *kNames[XR_NUM_VARIANTS] = {
-    "xoshiro256+", "xoshiro256++", "xoshiro256**", "xoroshiro128+", "xoroshiro128++",
-    "xoroshiro128**", "xoshiro128++", "xoshiro128**", "xoshiro128+"};
+    "xoshiro256+", "xoshiro256++", "xoshiro256**", "xoroshiro128+", "xoroshiro128++", "xoroshiro128**",
+    "xoshiro128++", "xoshiro128**", "xoshiro128+", "xoroshiro128*", "xoroshiro64*", "xoroshiro64**",
+    "xoshiro512+", "xoshiro512++", "xoshiro512**", "xoroshiro1024*", "xoroshiro1024++", "xoroshiro1024**"};
 
 static bool variant_ok(int v) { return v >= 0 && v < XR_NUM_VARIANTS; }
 
@@ -85,13 +104,13 @@ extern "C" uint64_t xr_launch_count(void) { return g_launches.load(std::memory_o
 extern "C" int xr_state_words(int variant)
 {
     if (!variant_ok(variant)) return -1;
-    return engine_of(variant) == ENG_XOSHIRO256 || engine_of(variant) == ENG_XOSHIRO128 ? 4 : 2;
+    return kEngineWords[engine_of(variant)];
 }
 
 extern "C" int xr_word_bits(int variant)
 {
     if (!variant_ok(variant)) return -1;
-    return engine_of(variant) == ENG_XOSHIRO128 ? 32 : 64;
+    return kEngineWordBits[engine_of(variant)];
 }
 
 extern "C" int xr_state_bytes(int variant)
@@ -164,8 +183,27 @@ static void pset_dists(int engine, int *d)
 }
 
 namespace xr {
+int ensure_engine(xr_ctx *ctx, int engine)
+{
+    if (ctx->tables[engine]) return XR_OK;
+    std::lock_guard<std::mutex> lk(*(std::mutex *)ctx->lazy_mutex);
+    if (ctx->tables[engine]) return XR_OK;
+    const size_t n = (size_t)engine_bits(engine);
+    uint32_t *t = nullptr;
+    cudaError_t e = cudaMalloc((void **)&t, n * n * n / 8);
+    if (e == cudaSuccess) e = launch_build_tables(engine, t, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(t);
+        return status_of(e);
+    }
+    ctx->tables[engine] = t;
+    return XR_OK;
+}
+
 int pset_index(int engine, int d)
 {
+    if (engine >= NUM_PSET_ENGINES) return -1;
     int dists[NUM_PSET_DISTS];
     pset_dists(engine, dists);
     for (int di = 0; di < NUM_PSET_DISTS; ++di)
@@ -200,6 +238,7 @@ extern "C" int xr_ctx_destroy(xr_ctx *ctx)
     }
     cudaFree(ctx->base_state);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    delete (std::mutex *)ctx->lazy_mutex;
     free(ctx);
     return XR_OK;
 }
@@ -212,6 +251,7 @@ extern "C" int xr_ctx_create(int device, xr_ctx **out)
     xr_ctx *ctx = (xr_ctx *)calloc(1, sizeof(xr_ctx));
     if (!ctx) return XR_ENOMEM;
     ctx->device = device;
+    ctx->lazy_mutex = new std::mutex();
     cudaDriverEntryPointQueryResult q;
     void *fn = NULL;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
@@ -220,7 +260,7 @@ extern "C" int xr_ctx_create(int device, xr_ctx **out)
         ctx->encode = (EncodeTiledFn)fn;
     cudaGetLastError();
     int rc = XR_OK;
-    for (int e = 0; e < NUM_ENGINES && rc == XR_OK; ++e) {
+    for (int e = 0; e < NUM_PSET_ENGINES && rc == XR_OK; ++e) {
         const size_t n = (size_t)engine_bits(e);
         rc = status_of(cudaMalloc((void **)&ctx->tables[e], n * n * n / 8));
         if (rc == XR_OK) rc = status_of(launch_build_tables(e, ctx->tables[e], 0));
@@ -261,6 +301,10 @@ extern "C" int xr_status(xr_ctx *ctx, int reset)
 extern "C" int xr_jump_table(xr_ctx *ctx, int variant, int k, void *h_out)
 {
     if (!ctx || !variant_ok(variant) || !h_out) return XR_EINVAL;
+    {
+        const int erc = ensure_engine(ctx, engine_of(variant));
+        if (erc != XR_OK) return erc;
+    }
     const int e = engine_of(variant);
     const size_t n = (size_t)engine_bits(e);
     if (k < 0 || (size_t)k >= n) return XR_EINVAL;
@@ -327,6 +371,10 @@ extern "C" int xr_jump(xr_ctx *ctx, int variant, int kind, void *d_states, size_
     if (!ctx || !variant_ok(variant) || (kind != XR_JUMP && kind != XR_LONG_JUMP)) return XR_EINVAL;
     if (count == 0 || times == 0) return XR_OK;
     if (!states_ok(d_states)) return XR_EINVAL;
+    {
+        const int erc = ensure_engine(ctx, engine_of(variant));
+        if (erc != XR_OK) return erc;
+    }
     const int e = engine_of(variant);
     return status_of(launch_apply_pow(e, ctx->tables[e], klist(times, xr_jump_log2(variant, kind), engine_bits(e)),
                                       d_states, count, (cudaStream_t)stream));
@@ -338,6 +386,10 @@ extern "C" int xr_advance(xr_ctx *ctx, int variant, void *d_states, size_t count
     if (!ctx || !variant_ok(variant)) return XR_EINVAL;
     if (count == 0 || nsteps == 0) return XR_OK;
     if (!states_ok(d_states)) return XR_EINVAL;
+    {
+        const int erc = ensure_engine(ctx, engine_of(variant));
+        if (erc != XR_OK) return erc;
+    }
     const int e = engine_of(variant);
     return status_of(launch_apply_pow(e, ctx->tables[e], klist(nsteps, 0, engine_bits(e)), d_states,
                                       count, (cudaStream_t)stream));
@@ -356,14 +408,9 @@ static cudaError_t make_streams(xr_ctx *ctx, int variant, int d, const void *d_b
         err = launch_apply_pow(e, ctx->tables[e], klist(first, d, engine_bits(e)), out, 1, st);
         if (err != cudaSuccess) return err;
     }
-    int dists[NUM_PSET_DISTS];
-    pset_dists(e, dists);
-    const size_t n = (size_t)engine_bits(e);
-    for (int di = 0; di < NUM_PSET_DISTS; ++di)
-        if (dists[di] == d && S <= ((size_t)1 << (PSET_BITS * PSET_LEVELS))) {
-            const size_t set_words = (size_t)PSET_SIZE * n * (n / 32);
-            return launch_streams_psets(e, ctx->psets[e] + (size_t)di * PSET_LEVELS * set_words, out, S, st);
-        }
+    const int di = pset_index(e, d);
+    if (di >= 0 && S <= ((size_t)1 << (PSET_BITS * PSET_LEVELS)))
+        return launch_streams_psets(e, pset_sets(ctx, e, di), out, S, st);
     return launch_tree(e, ctx->tables[e], d, out, S, st);
 }
 
@@ -376,6 +423,10 @@ extern "C" int xr_make_streams(xr_ctx *ctx, int variant, int kind, const void *d
     const size_t sb = (size_t)xr_state_bytes(variant);
     const char *b = (const char *)d_base, *o = (const char *)d_states_out;
     if (b < o + S * sb && o < b + sb) return XR_EINVAL;  // overlap
+    {
+        const int erc = ensure_engine(ctx, engine_of(variant));
+        if (erc != XR_OK) return erc;
+    }
     return status_of(make_streams(ctx, variant, xr_jump_log2(variant, kind), d_base, first, S,
                                   d_states_out, (cudaStream_t)stream));
 }
@@ -424,6 +475,10 @@ extern "C" int xr_fill_seq(xr_ctx *ctx, int variant, void *d_state, size_t n, in
     if (n == 0) return XR_OK;
     const size_t es = (size_t)xr_dtype_bytes(dtype);
     if (!states_ok(d_state) || !d_out || ((uintptr_t)d_out % es)) return XR_EINVAL;
+    {
+        const int erc = ensure_engine(ctx, engine_of(variant));
+        if (erc != XR_OK) return erc;
+    }
     const cudaStream_t st = (cudaStream_t)stream;
     const size_t seg = (size_t)1 << SEQ_LOG2;
     const size_t full = n / seg, tail = n % seg, P = full + (tail ? 1 : 0);
@@ -460,6 +515,10 @@ extern "C" int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_ba
     unsigned char any = 0;
     for (size_t b = 0; b < sb; ++b) any |= ((const unsigned char *)h_base)[b];
     if (!any) return XR_EZERO_STATE;
+    {
+        const int erc = ensure_engine(ctx, engine_of(variant));
+        if (erc != XR_OK) return erc;
+    }
     const cudaStream_t st = (cudaStream_t)stream;
     const size_t row = m * es;
     size_t ch = HOST_STAGING_BYTES / row;
@@ -543,6 +602,10 @@ extern "C" int xr_fill_seq_noalloc(xr_ctx *ctx, int variant, void *d_state, size
     if (n == 0) return XR_OK;
     const size_t es = (size_t)xr_dtype_bytes(dtype);
     if (!states_ok(d_state) || !d_out || ((uintptr_t)d_out % es)) return XR_EINVAL;
+    {
+        const int erc = ensure_engine(ctx, engine_of(variant));
+        if (erc != XR_OK) return erc;
+    }
     void *scratch = NULL;
     const int rc = noalloc_scratch(&scratch);
     if (rc != XR_OK) return rc;

@@ -60,27 +60,18 @@ __global__ void k_batch_seed(BatchDev d, size_t nreq)
     const BReq q = d.reqs[r];
     u32 w[SLOT_WORDS];
     u32 *slot = reinterpret_cast<u32 *>(d.slots + q.slot * 32);
-    const int eng = (q.variant <= 2) ? 0 : (q.variant <= 5 ? 1 : 3);
+    // 64-bit SplitMix64 outputs per state: 32-byte states take 4, 16-byte 2,
+    // 8-byte 1 (32-bit words take each output's low half first, so the u32
+    // words come out in the same order either way).
+    const int outs = q.variant <= 2 ? 4 : (q.variant <= 9 ? 2 : 1);
     if (d.seeds) {
         u64 x = d.seeds[r];
 #pragma unroll
         for (int j = 0; j < SLOT_WORDS; ++j) w[j] = 0u;
-        if (eng == 0) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const u64 z = splitmix64_next(x);
-                w[2 * j] = (u32)z;
-                w[2 * j + 1] = (u32)(z >> 32);
-            }
-        } else {
-            // xoroshiro128: two 64-bit words; xoshiro128: each output gives two
-            // 32-bit words, low half first -- the same four u32 words either way.
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const u64 z = splitmix64_next(x);
-                w[2 * j] = (u32)z;
-                w[2 * j + 1] = (u32)(z >> 32);
-            }
+        for (int j = 0; j < outs; ++j) {
+            const u64 z = splitmix64_next(x);
+            w[2 * j] = (u32)z;
+            w[2 * j + 1] = (u32)(z >> 32);
         }
         reinterpret_cast<uint4 *>(slot)[0] = make_uint4(w[0], w[1], w[2], w[3]);
         reinterpret_cast<uint4 *>(slot)[1] = make_uint4(w[4], w[5], w[6], w[7]);
@@ -89,7 +80,7 @@ __global__ void k_batch_seed(BatchDev d, size_t nreq)
         const uint4 b = reinterpret_cast<const uint4 *>(slot)[1];
         w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
         w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
-        if (eng != 0) w[4] = w[5] = w[6] = w[7] = 0u;
+        for (int j = 2 * outs; j < SLOT_WORDS; ++j) w[j] = 0u;
     }
     u32 any = 0;
 #pragma unroll
@@ -125,17 +116,13 @@ __global__ void __launch_bounds__(256)
     const u64 child = it.parent + (u64)j * stride;
     if (child >= it.limit) return;
     u32 v[NW], r[NW];
-    const uint4 *ps = reinterpret_cast<const uint4 *>(segstates + it.parent * SLOT_WORDS);
+    const u32 *ps = segstates + it.parent * SLOT_WORDS;
 #pragma unroll
-    for (int q = 0; q < NW / 4; ++q) {
-        const uint4 a = ps[q];
-        v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
-    }
+    for (int w = 0; w < NW; ++w) v[w] = ps[w];
     f2_matvec<NW, true>(M, v, r);
-    uint4 *cs = reinterpret_cast<uint4 *>(segstates + child * SLOT_WORDS);
+    u32 *cs = segstates + child * SLOT_WORDS;
 #pragma unroll
-    for (int q = 0; q < NW / 4; ++q) cs[q] = make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-    if (NW == 4) cs[1] = make_uint4(0u, 0u, 0u, 0u);
+    for (int w = 0; w < SLOT_WORDS; ++w) cs[w] = w < NW ? r[w % NW] : 0u;
 }
 
 // ---------------------------------------------------------------- persistent fill
@@ -293,6 +280,9 @@ __global__ void __launch_bounds__(512)
             XR_BATCH_CASE(6, DT_U32) XR_BATCH_CASE(6, DT_F64) XR_BATCH_CASE(6, DT_F32)
             XR_BATCH_CASE(7, DT_U32) XR_BATCH_CASE(7, DT_F64) XR_BATCH_CASE(7, DT_F32)
             XR_BATCH_CASE(8, DT_U32) XR_BATCH_CASE(8, DT_F64) XR_BATCH_CASE(8, DT_F32)
+            XR_BATCH_CASE(9, DT_U64) XR_BATCH_CASE(9, DT_F64) XR_BATCH_CASE(9, DT_F32)
+            XR_BATCH_CASE(10, DT_U32) XR_BATCH_CASE(10, DT_F64) XR_BATCH_CASE(10, DT_F32)
+            XR_BATCH_CASE(11, DT_U32) XR_BATCH_CASE(11, DT_F64) XR_BATCH_CASE(11, DT_F32)
         default:
             break;
         }
@@ -310,11 +300,12 @@ using namespace xr;
 namespace xr {
 
 static int es_of(int dtype) { return (dtype == XR_U64 || dtype == XR_F64) ? 8 : 4; }
+static bool word32(int v) { return (v >= 6 && v <= 8) || v == 10 || v == 11; }
 static bool dtype_ok_b(int v, int dt)
 {
     if (dt == XR_F64 || dt == XR_F32) return true;
-    if (dt == XR_U64) return v <= 5;
-    if (dt == XR_U32) return v >= 6;
+    if (dt == XR_U64) return !word32(v);
+    if (dt == XR_U32) return word32(v);
     return false;
 }
 
@@ -325,6 +316,7 @@ int check_requests(const xr_request *h, size_t nreq)
     for (size_t r = 0; r < nreq; ++r) {
         const xr_request &q = h[r];
         if (q.variant < 0 || q.variant >= XR_NUM_VARIANTS || !dtype_ok_b(q.variant, q.dtype)) return XR_EINVAL;
+        if (engine_of(q.variant) >= NUM_PSET_ENGINES) return XR_EUNSUPPORTED;  // states over 32 bytes
         if (q.out_offset % 16) return XR_EINVAL;
         if (q.n > (1ull << 50)) return XR_EINVAL;
         slots.push_back(q.slot);
@@ -415,7 +407,7 @@ void build_plan(const xr_request *in, size_t nreq, HostPlan &p)
     // levels of the segment-start scheme, per (level, engine)
     for (int l = PSET_LEVELS - 1; l >= 0; --l) {
         const u64 stride = 1ull << (PSET_BITS * l), span = stride << PSET_BITS;
-        for (int e = 0; e < NUM_ENGINES; ++e) {
+        for (int e = 0; e < NUM_PSET_ENGINES; ++e) {
             LevelLaunch L;
             L.engine = e;
             L.level = l;
@@ -570,8 +562,10 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
         const u64 stride = 1ull << (PSET_BITS * L.level);
         if (n == 256)
             k_batch_level<8><<<grid, 256, 0, st>>>(P, items + L.first, L.count, stride, dp.segstates);
-        else
+        else if (n == 128)
             k_batch_level<4><<<grid, 256, 0, st>>>(P, items + L.first, L.count, stride, dp.segstates);
+        else
+            k_batch_level<2><<<grid, 256, 0, st>>>(P, items + L.first, L.count, stride, dp.segstates);
         count_launch();
         err = cudaGetLastError();
     }

@@ -56,15 +56,60 @@ struct Xoroshiro2 {
     }
 };
 
+// xoshiro with eight words (Sec. 3.2), the columns of S_8w:
+//   s0' = s0 ^ s6          s1' = s0 ^ s1 ^ s2     s2' = s0 ^ s2        s3' = s3 ^ s4
+//   s4' = s1 ^ s4 ^ s5     s5' = s1 ^ s5          s6' = (s1 << A) ^ s3 ^ s6 ^ s7
+//   s7' = rotl(s3 ^ s7, B)
+template <typename W, int A, int B>
+struct Xoshiro8 {
+    typedef W word;
+    static constexpr int K = 8;
+    static constexpr int NBITS = 8 * 8 * (int)sizeof(W);
+    W s[8];
+    __device__ __forceinline__ void step()
+    {
+        const W n0 = s[0] ^ s[6], n1 = s[0] ^ s[1] ^ s[2], n2 = s[0] ^ s[2], n3 = s[3] ^ s[4];
+        const W n4 = s[1] ^ s[4] ^ s[5], n5 = s[1] ^ s[5], n6 = (s[1] << A) ^ s[3] ^ s[6] ^ s[7];
+        const W n7 = rotl(s[3] ^ s[7], B);
+        s[0] = n0; s[1] = n1; s[2] = n2; s[3] = n3; s[4] = n4; s[5] = n5; s[6] = n6; s[7] = n7;
+    }
+};
+
+// xoroshiro with sixteen words (Eq. (M), X_kw with k = 16), written with the
+// words shifting down one place per step (the figure's cyclic index becomes
+// register renaming once 16 steps are unrolled):
+//   t = s0 ^ s15;  s_j' = s_{j+1} (j <= 13);  s14' = rotl(s0, A) ^ t ^ (t << B);
+//   s15' = rotl(t, C)
+template <typename W, int A, int B, int C>
+struct Xoroshiro16 {
+    typedef W word;
+    static constexpr int K = 16;
+    static constexpr int NBITS = 16 * 8 * (int)sizeof(W);
+    W s[16];
+    __device__ __forceinline__ void step()
+    {
+        const W t = s[0] ^ s[15];
+        const W n14 = rotl(s[0], A) ^ t ^ (t << B);
+        const W n15 = rotl(t, C);
+#pragma unroll
+        for (int j = 0; j < 14; ++j) s[j] = s[j + 1];
+        s[14] = n14;
+        s[15] = n15;
+    }
+};
+
 // Engine ids used for the jump tables.
 enum { ENG_XOSHIRO256 = 0, ENG_XOROSHIRO128 = 1, ENG_XOROSHIRO128PP = 2, ENG_XOSHIRO128 = 3,
-       NUM_ENGINES = 4 };
+       ENG_XOROSHIRO64 = 4, ENG_XOSHIRO512 = 5, ENG_XOROSHIRO1024 = 6, NUM_ENGINES = 7 };
 
 template <int ENG> struct EngineOf;
 template <> struct EngineOf<ENG_XOSHIRO256> { typedef Xoshiro4<u64, 17, 45> type; };      // Table 4
 template <> struct EngineOf<ENG_XOROSHIRO128> { typedef Xoroshiro2<u64, 24, 16, 37> type; };  // Table 4
 template <> struct EngineOf<ENG_XOROSHIRO128PP> { typedef Xoroshiro2<u64, 49, 21, 28> type; };// Table 4
 template <> struct EngineOf<ENG_XOSHIRO128> { typedef Xoshiro4<u32, 9, 11> type; };        // Table 7
+template <> struct EngineOf<ENG_XOROSHIRO64> { typedef Xoroshiro2<u32, 26, 9, 13> type; };  // Table 7
+template <> struct EngineOf<ENG_XOSHIRO512> { typedef Xoshiro8<u64, 11, 21> type; };       // Table 4
+template <> struct EngineOf<ENG_XOROSHIRO1024> { typedef Xoroshiro16<u64, 25, 27, 36> type; };  // Table 4
 
 // ---------------------------------------------------------------- generators
 // Scrambler applied to the current state (Sec. 2), parameters of Tables 5, 8.
@@ -87,33 +132,66 @@ XR_GEN(5, ENG_XOROSHIRO128, return rotl(e.s[0] * 5ull, 7) * 9ull;)             /
 XR_GEN(6, ENG_XOSHIRO128, return rotl(e.s[0] + e.s[3], 7) + e.s[0];)           // xoshiro128++
 XR_GEN(7, ENG_XOSHIRO128, return rotl(e.s[1] * 5u, 7) * 9u;)                   // xoshiro128**
 XR_GEN(8, ENG_XOSHIRO128, return e.s[0] + e.s[3];)                              // xoshiro128+
+XR_GEN(9, ENG_XOROSHIRO128, return e.s[0] * 0x9e3779b97f4a7c13ull;)             // xoroshiro128*
+XR_GEN(10, ENG_XOROSHIRO64, return e.s[0] * 0x9E3779BBu;)                       // xoroshiro64*
+XR_GEN(11, ENG_XOROSHIRO64, return rotl(e.s[0] * 0x9E3779BBu, 5) * 5u;)         // xoroshiro64**
+XR_GEN(12, ENG_XOSHIRO512, return e.s[0] + e.s[2];)                             // xoshiro512+
+XR_GEN(13, ENG_XOSHIRO512, return rotl(e.s[0] + e.s[2], 17) + e.s[2];)         // xoshiro512++
+XR_GEN(14, ENG_XOSHIRO512, return rotl(e.s[1] * 5ull, 7) * 9ull;)              // xoshiro512**
+XR_GEN(15, ENG_XOROSHIRO1024, return e.s[0] * 0x9e3779b97f4a7c13ull;)           // xoroshiro1024*
+XR_GEN(16, ENG_XOROSHIRO1024, return rotl(e.s[0] + e.s[15], 23) + e.s[15];)    // xoroshiro1024++
+XR_GEN(17, ENG_XOROSHIRO1024, return rotl(e.s[0] * 5ull, 7) * 9ull;)           // xoroshiro1024**
 #undef XR_GEN
 
 // ---------------------------------------------------------------- state I/O
-// A state in memory is its words in order, little-endian; 32 B or 16 B.
+// A state in memory is its words in order, little-endian: 8 to 128 bytes,
+// aligned to its size (16 bytes at most).
 template <typename E>
 __device__ __forceinline__ void load_state(E &e, const void *p)
 {
-    if (sizeof(e.s) == 32) {
-        const uint4 a = reinterpret_cast<const uint4 *>(p)[0];
-        const uint4 b = reinterpret_cast<const uint4 *>(p)[1];
-        u64 *w = reinterpret_cast<u64 *>(&e.s[0]);
-        w[0] = (u64)a.x | ((u64)a.y << 32); w[1] = (u64)a.z | ((u64)a.w << 32);
-        w[2] = (u64)b.x | ((u64)b.y << 32); w[3] = (u64)b.z | ((u64)b.w << 32);
+    constexpr int B = (int)sizeof(e.s);
+    u32 w[B / 4];
+    if constexpr (B >= 16) {
+#pragma unroll
+        for (int q = 0; q < B / 16; ++q) {
+            const uint4 a = reinterpret_cast<const uint4 *>(p)[q];
+            w[4 * q] = a.x; w[4 * q + 1] = a.y; w[4 * q + 2] = a.z; w[4 * q + 3] = a.w;
+        }
     } else {
-        const uint4 a = reinterpret_cast<const uint4 *>(p)[0];
-        u32 *w = reinterpret_cast<u32 *>(&e.s[0]);
-        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+        const uint2 a = reinterpret_cast<const uint2 *>(p)[0];
+        w[0] = a.x; w[1] = a.y;
+    }
+    if constexpr (sizeof(typename E::word) == 8) {
+#pragma unroll
+        for (int j = 0; j < E::K; ++j) e.s[j] = (u64)w[2 * j] | ((u64)w[2 * j + 1] << 32);
+    } else {
+#pragma unroll
+        for (int j = 0; j < E::K; ++j) e.s[j] = w[j];
     }
 }
 
 template <typename E>
 __device__ __forceinline__ void store_state(const E &e, void *p)
 {
-    const u32 *w = reinterpret_cast<const u32 *>(&e.s[0]);
-    uint4 *q = reinterpret_cast<uint4 *>(p);
-    q[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    if (sizeof(e.s) == 32) q[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    constexpr int B = (int)sizeof(e.s);
+    u32 w[B / 4];
+    if constexpr (sizeof(typename E::word) == 8) {
+#pragma unroll
+        for (int j = 0; j < E::K; ++j) {
+            w[2 * j] = (u32)e.s[j];
+            w[2 * j + 1] = (u32)(e.s[j] >> 32);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < E::K; ++j) w[j] = e.s[j];
+    }
+    if constexpr (B >= 16) {
+#pragma unroll
+        for (int q = 0; q < B / 16; ++q)
+            reinterpret_cast<uint4 *>(p)[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    } else {
+        reinterpret_cast<uint2 *>(p)[0] = make_uint2(w[0], w[1]);
+    }
 }
 
 // State <-> its n / 32 little-endian u32 words held in registers.
@@ -296,15 +374,24 @@ __device__ __forceinline__ void f2_matvec(const u32 *__restrict__ M, const u32 (
         for (int b = 0; b < 32; ++b) {
             const u32 mask = (u32)((int)(bits << (31 - b)) >> 31);
             const uint4 *col = reinterpret_cast<const uint4 *>(M + (size_t)(w * 32 + b) * NW);
+            if constexpr (NW >= 4) {
 #pragma unroll
-            for (int q = 0; q < NW / 4; ++q) {
-                uint4 c;
-                if (SHARED) c = col[q];
-                else c = __ldg(col + q);
-                acc[4 * q + 0] ^= c.x & mask;
-                acc[4 * q + 1] ^= c.y & mask;
-                acc[4 * q + 2] ^= c.z & mask;
-                acc[4 * q + 3] ^= c.w & mask;
+                for (int q = 0; q < NW / 4; ++q) {
+                    uint4 c;
+                    if (SHARED) c = col[q];
+                    else c = __ldg(col + q);
+                    acc[4 * q + 0] ^= c.x & mask;
+                    acc[4 * q + 1] ^= c.y & mask;
+                    acc[4 * q + 2] ^= c.z & mask;
+                    acc[4 * q + 3] ^= c.w & mask;
+                }
+            } else {
+                const uint2 *col2 = reinterpret_cast<const uint2 *>(col);
+                uint2 c;
+                if (SHARED) c = col2[0];
+                else c = __ldg(col2);
+                acc[0] ^= c.x & mask;
+                acc[1] ^= c.y & mask;
             }
         }
     }

@@ -18,8 +18,11 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 // Count one kernel launch (host-side, process-wide).
 void count_launch();
 
-// Number of engines (xoshiro256, xoroshiro128, xoroshiro128 for ++, xoshiro128).
-constexpr int NUM_ENGINES_H = 4;
+// Number of engines (xoshiro256, xoroshiro128, xoroshiro128 for ++, xoshiro128,
+// xoroshiro64, xoshiro512, xoroshiro1024) and how many of them (the first
+// ones, states of 256 bits or less) have power sets and serve batches.
+constexpr int NUM_ENGINES_H = 7;
+constexpr int NUM_PSET_ENGINES = 5;
 
 // Engine of each variant and its state size in bits.
 int engine_of(int variant);
@@ -87,9 +90,13 @@ struct xr_ctx {
     cudaStream_t side;        // copy stream of xr_fill_host
     cudaEvent_t ev_gen[2], ev_copy[2];
     xr::EncodeTiledFn encode;
+    void *lazy_mutex;         // guards the lazy build of the large engines' tables
 };
 
 namespace xr {
+// Build the jump tables of an engine if it has none yet (large engines are
+// built on first use); XR_OK or an error status.
+int ensure_engine(xr_ctx *ctx, int engine);
 // Index of the power sets of distance log2 d for an engine (-1 if none).
 int pset_index(int engine, int d);
 // The three level sets of distance index di of an engine.

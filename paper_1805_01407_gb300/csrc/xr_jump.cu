@@ -12,6 +12,35 @@
 
 namespace xr {
 
+// ---------------------------------------------------------------- vectors
+
+template <int NW>
+__device__ __forceinline__ void load_vec(u32 (&v)[NW], const u32 *p)
+{
+    if constexpr (NW >= 4) {
+#pragma unroll
+        for (int q = 0; q < NW / 4; ++q) {
+            const uint4 a = reinterpret_cast<const uint4 *>(p)[q];
+            v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+        }
+    } else {
+        const uint2 a = reinterpret_cast<const uint2 *>(p)[0];
+        v[0] = a.x; v[1] = a.y;
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void store_vec(const u32 (&v)[NW], u32 *p)
+{
+    if constexpr (NW >= 4) {
+#pragma unroll
+        for (int q = 0; q < NW / 4; ++q)
+            reinterpret_cast<uint4 *>(p)[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+        reinterpret_cast<uint2 *>(p)[0] = make_uint2(v[0], v[1]);
+    }
+}
+
 // ---------------------------------------------------------------- table build
 
 // Column c of T is the step of the unit state e_c (bit c set).
@@ -60,6 +89,21 @@ __global__ void __launch_bounds__(NW * 32) k_square_chain(u32 *tables)
     }
 }
 
+// For the large engines (512 and 1024 bits) one launch per power: column c
+// of T^(2^(k+1)) = T^(2^k) (column c of T^(2^k)), the matrix read through
+// the read-only cache with warp-uniform loads.
+template <int NW>
+__global__ void __launch_bounds__(128) k_square_step(const u32 *__restrict__ A, u32 *B)
+{
+    constexpr int n = NW * 32;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    u32 v[NW], r[NW];
+    load_vec<NW>(v, A + (size_t)c * NW);
+    f2_matvec<NW, false>(A, v, r);
+    store_vec<NW>(r, B + (size_t)c * NW);
+}
+
 template <int ENG>
 static cudaError_t build_tables_e(uint32_t *tables, cudaStream_t stream)
 {
@@ -69,9 +113,19 @@ static cudaError_t build_tables_e(uint32_t *tables, cudaStream_t stream)
     count_launch();
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    k_square_chain<NW><<<1, n, 0, stream>>>(tables);
-    count_launch();
-    return cudaGetLastError();
+    if constexpr (NW <= 8) {
+        k_square_chain<NW><<<1, n, 0, stream>>>(tables);
+        count_launch();
+        return cudaGetLastError();
+    } else {
+        const size_t mat = (size_t)n * NW;
+        for (int k = 0; k + 1 < n && err == cudaSuccess; ++k) {
+            k_square_step<NW><<<n / 128, 128, 0, stream>>>(tables + k * mat, tables + (k + 1) * mat);
+            count_launch();
+            err = cudaGetLastError();
+        }
+        return err;
+    }
 }
 
 cudaError_t launch_build_tables(int engine, uint32_t *tables, cudaStream_t stream)
@@ -81,29 +135,15 @@ cudaError_t launch_build_tables(int engine, uint32_t *tables, cudaStream_t strea
     case ENG_XOROSHIRO128: return build_tables_e<ENG_XOROSHIRO128>(tables, stream);
     case ENG_XOROSHIRO128PP: return build_tables_e<ENG_XOROSHIRO128PP>(tables, stream);
     case ENG_XOSHIRO128: return build_tables_e<ENG_XOSHIRO128>(tables, stream);
+    case ENG_XOROSHIRO64: return build_tables_e<ENG_XOROSHIRO64>(tables, stream);
+    case ENG_XOSHIRO512: return build_tables_e<ENG_XOSHIRO512>(tables, stream);
+    case ENG_XOROSHIRO1024: return build_tables_e<ENG_XOROSHIRO1024>(tables, stream);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // ---------------------------------------------------------------- apply powers
 
-template <int NW>
-__device__ __forceinline__ void load_vec(u32 (&v)[NW], const u32 *p)
-{
-#pragma unroll
-    for (int q = 0; q < NW / 4; ++q) {
-        const uint4 a = reinterpret_cast<const uint4 *>(p)[q];
-        v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
-    }
-}
-
-template <int NW>
-__device__ __forceinline__ void store_vec(const u32 (&v)[NW], u32 *p)
-{
-#pragma unroll
-    for (int q = 0; q < NW / 4; ++q)
-        reinterpret_cast<uint4 *>(p)[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-}
 
 template <int NW>
 __global__ void __launch_bounds__(128)
@@ -128,10 +168,13 @@ cudaError_t launch_apply_pow(int engine, const uint32_t *tables, const KList &ks
 {
     if (count == 0 || ks.n == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((count + 127) / 128);
-    if (engine_bits(engine) == 256)
-        k_apply_pow<8><<<grid, 128, 0, stream>>>(tables, ks, (u32 *)states, count);
-    else
-        k_apply_pow<4><<<grid, 128, 0, stream>>>(tables, ks, (u32 *)states, count);
+    switch (engine_bits(engine)) {
+    case 1024: k_apply_pow<32><<<grid, 128, 0, stream>>>(tables, ks, (u32 *)states, count); break;
+    case 512: k_apply_pow<16><<<grid, 128, 0, stream>>>(tables, ks, (u32 *)states, count); break;
+    case 256: k_apply_pow<8><<<grid, 128, 0, stream>>>(tables, ks, (u32 *)states, count); break;
+    case 128: k_apply_pow<4><<<grid, 128, 0, stream>>>(tables, ks, (u32 *)states, count); break;
+    default: k_apply_pow<2><<<grid, 128, 0, stream>>>(tables, ks, (u32 *)states, count); break;
+    }
     count_launch();
     return cudaGetLastError();
 }
@@ -140,23 +183,34 @@ cudaError_t launch_apply_pow(int engine, const uint32_t *tables, const KList &ks
 
 // Levels L while 2^L < min(S, 2 * blockDim): one CTA, the level matrix staged
 // in shared memory, a barrier between levels.
+// The level matrix is staged in shared memory for states up to 512 bits;
+// the 1024-bit one (128 KiB) is read through the read-only cache instead.
+template <int NW>
+struct TreeStage {
+    static constexpr bool on = NW <= 16;
+    static constexpr int words = on ? NW * 32 * NW : 4;
+};
+
 template <int NW>
 __global__ void __launch_bounds__(256)
     k_tree_small(const u32 *__restrict__ tables, int kbase, u32 *states, size_t S, int levels)
 {
     constexpr int n = NW * 32;
-    __shared__ __align__(16) u32 M[n * NW];
+    __shared__ __align__(16) u32 M[TreeStage<NW>::words];
     for (int L = 0; L < levels; ++L) {
         const u32 *src = tables + (size_t)((kbase + L) % n) * n * NW;
-        for (int t = threadIdx.x; t < n * NW / 4; t += blockDim.x)
-            reinterpret_cast<uint4 *>(M)[t] = reinterpret_cast<const uint4 *>(src)[t];
+        if (TreeStage<NW>::on) {
+            for (int t = threadIdx.x; t < n * NW / 4; t += blockDim.x)
+                reinterpret_cast<uint4 *>(M)[t] = reinterpret_cast<const uint4 *>(src)[t];
+        }
         __syncthreads();
         const size_t half = (size_t)1 << L;
         const size_t idx = threadIdx.x;
         if (idx < half && half + idx < S) {
             u32 v[NW], r[NW];
             load_vec<NW>(v, states + idx * NW);
-            f2_matvec<NW, true>(M, v, r);
+            if (TreeStage<NW>::on) f2_matvec<NW, true>(M, v, r);
+            else f2_matvec<NW, false>(src, v, r);
             store_vec<NW>(r, states + (half + idx) * NW);
         }
         __syncthreads();
@@ -169,15 +223,18 @@ __global__ void __launch_bounds__(256)
     k_tree_level(const u32 *__restrict__ Mg, u32 *states, size_t half, size_t S)
 {
     constexpr int n = NW * 32;
-    __shared__ __align__(16) u32 M[n * NW];
-    for (int t = threadIdx.x; t < n * NW / 4; t += blockDim.x)
-        reinterpret_cast<uint4 *>(M)[t] = reinterpret_cast<const uint4 *>(Mg)[t];
+    __shared__ __align__(16) u32 M[TreeStage<NW>::words];
+    if (TreeStage<NW>::on) {
+        for (int t = threadIdx.x; t < n * NW / 4; t += blockDim.x)
+            reinterpret_cast<uint4 *>(M)[t] = reinterpret_cast<const uint4 *>(Mg)[t];
+    }
     __syncthreads();
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= half || half + idx >= S) return;
     u32 v[NW], r[NW];
     load_vec<NW>(v, states + idx * NW);
-    f2_matvec<NW, true>(M, v, r);
+    if (TreeStage<NW>::on) f2_matvec<NW, true>(M, v, r);
+    else f2_matvec<NW, false>(Mg, v, r);
     store_vec<NW>(r, states + (half + idx) * NW);
 }
 
@@ -209,8 +266,13 @@ static cudaError_t tree_nw(const uint32_t *tables, int kbase, void *states, size
 cudaError_t launch_tree(int engine, const uint32_t *tables, int kbase, void *states, size_t S,
                         cudaStream_t stream)
 {
-    if (engine_bits(engine) == 256) return tree_nw<8>(tables, kbase, states, S, stream);
-    return tree_nw<4>(tables, kbase, states, S, stream);
+    switch (engine_bits(engine)) {
+    case 1024: return tree_nw<32>(tables, kbase, states, S, stream);
+    case 512: return tree_nw<16>(tables, kbase, states, S, stream);
+    case 256: return tree_nw<8>(tables, kbase, states, S, stream);
+    case 128: return tree_nw<4>(tables, kbase, states, S, stream);
+    default: return tree_nw<2>(tables, kbase, states, S, stream);
+    }
 }
 
 // ---------------------------------------------------------------- power sets
@@ -266,13 +328,15 @@ cudaError_t launch_build_power_sets(int engine, const uint32_t *tables, const in
         for (int l = 0; l < PSET_LEVELS; ++l) kf.k[di * PSET_LEVELS + l] = (dists[di] + PSET_BITS * l) % n;
     const int nsets = kf.n;
     if (n == 256) k_pset_identity<8><<<nsets, 256, 0, stream>>>((u32 *)sets);
-    else k_pset_identity<4><<<nsets, 128, 0, stream>>>((u32 *)sets);
+    else if (n == 128) k_pset_identity<4><<<nsets, 128, 0, stream>>>((u32 *)sets);
+    else k_pset_identity<2><<<nsets, 64, 0, stream>>>((u32 *)sets);
     count_launch();
     cudaError_t err = cudaGetLastError();
     for (int L = 0; L < PSET_BITS && err == cudaSuccess; ++L) {
         const dim3 grid(1u << L, (unsigned)nsets);
         if (n == 256) k_pset_level<8><<<grid, 256, 0, stream>>>(tables, (u32 *)sets, kf, L);
-        else k_pset_level<4><<<grid, 128, 0, stream>>>(tables, (u32 *)sets, kf, L);
+        else if (n == 128) k_pset_level<4><<<grid, 128, 0, stream>>>(tables, (u32 *)sets, kf, L);
+        else k_pset_level<2><<<grid, 64, 0, stream>>>(tables, (u32 *)sets, kf, L);
         count_launch();
         err = cudaGetLastError();
     }
@@ -319,7 +383,8 @@ cudaError_t launch_streams_psets(int engine, const uint32_t *sets3, void *states
         const dim3 grid((unsigned)((nparents + 255) / 256), PSET_SIZE - 1);
         const uint32_t *P = sets3 + (size_t)l * set_words;
         if (n == 256) k_streams_level<8><<<grid, 256, 0, stream>>>(P, (u32 *)states, S, stride, nparents);
-        else k_streams_level<4><<<grid, 256, 0, stream>>>(P, (u32 *)states, S, stride, nparents);
+        else if (n == 128) k_streams_level<4><<<grid, 256, 0, stream>>>(P, (u32 *)states, S, stride, nparents);
+        else k_streams_level<2><<<grid, 256, 0, stream>>>(P, (u32 *)states, S, stride, nparents);
         count_launch();
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
@@ -369,12 +434,14 @@ cudaError_t launch_seed(int variant, const uint64_t *d_seeds, uint64_t seed, siz
     const unsigned grid = (unsigned)((count + 127) / 128);
     const int eng = engine_of(variant);
     const u64 *sp = (const u64 *)d_seeds;
-    if (eng == ENG_XOSHIRO256)
-        k_seed<8, 4><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status);
-    else if (eng == ENG_XOSHIRO128)
-        k_seed<4, 4><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status);
-    else
-        k_seed<8, 2><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status);
+    switch (eng) {
+    case ENG_XOSHIRO256: k_seed<8, 4><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status); break;
+    case ENG_XOSHIRO128: k_seed<4, 4><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status); break;
+    case ENG_XOROSHIRO64: k_seed<4, 2><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status); break;
+    case ENG_XOSHIRO512: k_seed<8, 8><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status); break;
+    case ENG_XOROSHIRO1024: k_seed<8, 16><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status); break;
+    default: k_seed<8, 2><<<grid, 128, 0, stream>>>(sp, seed, count, (u32 *)states, status); break;
+    }
     count_launch();
     return cudaGetLastError();
 }

@@ -35,7 +35,7 @@ struct AdmitReq {
     u64 n, slot;
 };
 struct Tables4 {
-    const u32 *t[4];
+    const u32 *t[NUM_PSET_ENGINES];
 };
 
 // State words of a client slot (32 bytes) <- SplitMix64(seed), by engine.
@@ -47,7 +47,7 @@ __global__ void k_server_seed(const int *variants, const u64 *seeds, u32 nclient
     u32 w[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) w[j] = 0u;
-    const int words64 = variants[c] <= 2 ? 4 : 2;
+    const int words64 = variants[c] <= 2 ? 4 : (variants[c] <= 9 ? 2 : 1);
     for (int j = 0; j < words64; ++j) {
         const u64 z = splitmix64_next(x);
         w[2 * j] = (u32)z;
@@ -70,14 +70,21 @@ __device__ __forceinline__ void warp_matvec(const u32 *__restrict__ M, u32 (&v)[
 #pragma unroll
     for (int k = 0; k < NW; ++k) {
         const u32 mask = 0u - ((v[k] >> lane) & 1u);
-        const uint4 *col = reinterpret_cast<const uint4 *>(M + (size_t)(k * 32 + lane) * NW);
+        const u32 *colp = M + (size_t)(k * 32 + lane) * NW;
+        if constexpr (NW >= 4) {
+            const uint4 *col = reinterpret_cast<const uint4 *>(colp);
 #pragma unroll
-        for (int q = 0; q < NW / 4; ++q) {
-            const uint4 c = __ldg(col + q);
-            acc[4 * q] ^= c.x & mask;
-            acc[4 * q + 1] ^= c.y & mask;
-            acc[4 * q + 2] ^= c.z & mask;
-            acc[4 * q + 3] ^= c.w & mask;
+            for (int q = 0; q < NW / 4; ++q) {
+                const uint4 c = __ldg(col + q);
+                acc[4 * q] ^= c.x & mask;
+                acc[4 * q + 1] ^= c.y & mask;
+                acc[4 * q + 2] ^= c.z & mask;
+                acc[4 * q + 3] ^= c.w & mask;
+            }
+        } else {
+            const uint2 c = __ldg(reinterpret_cast<const uint2 *>(colp));
+            acc[0] ^= c.x & mask;
+            acc[1] ^= c.y & mask;
         }
     }
 #pragma unroll
@@ -119,10 +126,9 @@ __device__ void admit_chain(const u32 *psets0, const u32 *tables, u32 *cstate, c
     for (u32 i = 0; i < count; ++i) {
         const AdmitReq q = reqs[first + i];
         if (lane == 0) {
-            uint4 *d = reinterpret_cast<uint4 *>(rslots + q.slot * 32);
+            u32 *d = reinterpret_cast<u32 *>(rslots + q.slot * 32);
 #pragma unroll
-            for (int k = 0; k < NW / 4; ++k) d[k] = make_uint4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-            if (NW == 4) d[1] = make_uint4(0u, 0u, 0u, 0u);
+            for (int w = 0; w < 8; ++w) d[w] = w < NW ? v[w % NW] : 0u;
         }
         warp_advance<NW>(psets0, tables, v, q.n, lane);
     }
@@ -142,6 +148,7 @@ __global__ void k_admit(Tables4 T, Tables4 P0, const AdmitClient *clients, u32 n
     const AdmitClient c = clients[i];
     u32 *cs = cstates + (size_t)c.client * 8;
     if (c.engine == 0) admit_chain<8>(P0.t[0], T.t[0], cs, reqs, c.first, c.count, rslots, lane);
+    else if (c.engine == ENG_XOROSHIRO64) admit_chain<2>(P0.t[c.engine], T.t[c.engine], cs, reqs, c.first, c.count, rslots, lane);
     else admit_chain<4>(P0.t[c.engine], T.t[c.engine], cs, reqs, c.first, c.count, rslots, lane);
 }
 
@@ -152,6 +159,7 @@ __global__ void k_admit_one(Tables4 T, Tables4 P0, u32 client, u32 engine, u64 n
     const int lane = threadIdx.x & 31;
     u32 *cs = cstates + (size_t)client * 8;
     if (engine == 0) admit_chain<8>(P0.t[0], T.t[0], cs, &q, 0, 1, slot, lane);
+    else if (engine == ENG_XOROSHIRO64) admit_chain<2>(P0.t[engine], T.t[engine], cs, &q, 0, 1, slot, lane);
     else admit_chain<4>(P0.t[engine], T.t[engine], cs, &q, 0, 1, slot, lane);
 }
 
@@ -283,7 +291,7 @@ static int sst(cudaError_t e)
 static Tables4 tables_of(xr_ctx *ctx)
 {
     Tables4 T;
-    for (int e = 0; e < 4; ++e) T.t[e] = ctx->tables[e];
+    for (int e = 0; e < NUM_PSET_ENGINES; ++e) T.t[e] = ctx->tables[e];
     return T;
 }
 
@@ -291,7 +299,7 @@ static Tables4 tables_of(xr_ctx *ctx)
 static Tables4 steps_of(xr_ctx *ctx)
 {
     Tables4 T;
-    for (int e = 0; e < 4; ++e) T.t[e] = pset_sets(ctx, e, pset_index(e, 0));
+    for (int e = 0; e < NUM_PSET_ENGINES; ++e) T.t[e] = pset_sets(ctx, e, pset_index(e, 0));
     return T;
 }
 
@@ -533,8 +541,10 @@ extern "C" int xr_server_create(xr_ctx *ctx, const xr_server_config *cfg, const 
     if (cfg->mode != XR_SERVE_BATCHED && cfg->mode != XR_SERVE_PLAIN) return XR_EINVAL;
     if (cfg->outputs_per_row && batch_smem_bytes(cfg->outputs_per_row, cfg->block ? cfg->block : 128) > 227 * 1024)
         return XR_EINVAL;
-    for (u32 c = 0; c < cfg->nclients; ++c)
+    for (u32 c = 0; c < cfg->nclients; ++c) {
         if (h_client_variants[c] < 0 || h_client_variants[c] >= XR_NUM_VARIANTS) return XR_EINVAL;
+        if (engine_of(h_client_variants[c]) >= NUM_PSET_ENGINES) return XR_EUNSUPPORTED;  // states over 32 bytes
+    }
     xr_server *s = new xr_server();
     s->ctx = ctx;
     s->cfg = *cfg;
@@ -603,7 +613,8 @@ static int submit(xr_server *s, uint32_t client, uint64_t n, int dtype, bool aut
 {
     if (!s || client >= s->cfg.nclients) return XR_EINVAL;
     const int v = s->cvar[client];
-    const bool ok = dtype == XR_F64 || dtype == XR_F32 || (dtype == XR_U64 && v <= 5) || (dtype == XR_U32 && v >= 6);
+    const bool w32 = xr_word_bits(v) == 32;
+    const bool ok = dtype == XR_F64 || dtype == XR_F32 || (dtype == XR_U64 && !w32) || (dtype == XR_U32 && w32);
     if (!ok) return XR_EINVAL;
     const u64 bytes = n * (u64)es_of_dtype(dtype);
     if (n == 0 || bytes + Arena::G > s->cfg.arena_bytes) return XR_EINVAL;

@@ -42,6 +42,9 @@ def test_properties(libxr):
         "xoshiro256+": (4, 64, 256), "xoshiro256++": (4, 64, 256), "xoshiro256**": (4, 64, 256),
         "xoroshiro128+": (2, 64, 128), "xoroshiro128++": (2, 64, 128), "xoroshiro128**": (2, 64, 128),
         "xoshiro128++": (4, 32, 128), "xoshiro128**": (4, 32, 128), "xoshiro128+": (4, 32, 128),
+        "xoroshiro128*": (2, 64, 128), "xoroshiro64*": (2, 32, 64), "xoroshiro64**": (2, 32, 64),
+        "xoshiro512+": (8, 64, 512), "xoshiro512++": (8, 64, 512), "xoshiro512**": (8, 64, 512),
+        "xoroshiro1024*": (16, 64, 1024), "xoroshiro1024++": (16, 64, 1024), "xoroshiro1024**": (16, 64, 1024),
     }
     for name, v in xr.VARIANTS.items():
         assert libxr.xr_variant_name(v).decode() == name

@@ -29,10 +29,9 @@ def ctx(xr):
 
 def slot_state(name, slots_np, slot):
     """Oracle words of a 32-byte slot (uint8 numpy array of all slots)."""
-    b = slots_np[slot * 32: slot * 32 + 32].tobytes()
-    if O.word_bits(name) == 32:
-        return np.frombuffer(b[:16], dtype=np.uint32).astype(np.uint64)
-    return np.frombuffer(b[:8 * O.state_words(name)], dtype=np.uint64).copy()
+    k, w = O.state_words(name), O.word_bits(name)
+    b = slots_np[slot * 32: slot * 32 + k * w // 8].tobytes()
+    return np.frombuffer(b, dtype=np.uint32 if w == 32 else np.uint64).astype(np.uint64)
 
 
 def request_view(out_np, off, n, dtype):
@@ -45,7 +44,7 @@ def small_mix(nreq, max_len, seed):
     rng = np.random.default_rng(seed)
     specs = []
     for r in range(nreq):
-        name = W.ALL_VARIANTS[int(rng.integers(0, len(W.ALL_VARIANTS)))]
+        name = W.SLOT_VARIANTS[int(rng.integers(0, len(W.SLOT_VARIANTS)))]
         dt = [W.native_dtype(name), "f64", "f32"][int(rng.integers(0, 3))]
         n = int(np.clip(np.floor(np.exp(rng.uniform(0, np.log(max_len + 1)))), 0, max_len))
         if r % 17 == 0:
@@ -177,6 +176,9 @@ def test_batch_rejects_bad_plans(ctx, xr):
         xr.Batch(ctx, [R(0, 0, 10, 0, 8)])                                # unaligned offset
     with pytest.raises(xr.XRError):
         xr.Batch(ctx, [R(6, 0, 10, 0, 0)])                                # u64 from a 32-bit generator
+    with pytest.raises(xr.XRError) as e:
+        xr.Batch(ctx, [R(xr.VARIANTS["xoshiro512+"], 0, 10, 0, 0)])      # 64-byte state: no slot fits
+    assert e.value.status == xr.XR_EUNSUPPORTED
 
 
 def test_batch_configuration_sampled(ctx, xr):

@@ -31,7 +31,7 @@ def ctx(xr):
 
 
 CLIENTS = ["xoshiro256**", "xoroshiro128++", "xoshiro256+", "xoroshiro128**", "xoshiro128++", "xoshiro128**",
-           "xoshiro256++", "xoroshiro128+"]
+           "xoshiro256++", "xoroshiro128+", "xoroshiro128*", "xoroshiro64**"]
 
 
 def mixed_trace(nreq, seed, max_len=1 << 17):
@@ -158,6 +158,9 @@ def test_rejects_bad_requests(ctx, xr):
             srv.submit(0, 1 << 20, "u64")                # larger than the arena
         with pytest.raises(xr.XRError):
             srv.release(12345)
+    with pytest.raises(xr.XRError) as e:
+        xr.Server(ctx, ["xoroshiro1024++"], [1], arena_bytes=1 << 20)   # 128-byte state: no slot fits
+    assert e.value.status == xr.XR_EUNSUPPORTED
 
 
 def test_serving_trace_sampled(ctx, xr):

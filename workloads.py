@@ -17,7 +17,12 @@ BULK_VARIANTS = (
     "xoroshiro128+", "xoroshiro128++", "xoroshiro128**",
     "xoshiro128**", "xoshiro128++",
 )
-ALL_VARIANTS = BULK_VARIANTS + ("xoshiro128+",)
+# The other generators of the paper's Sec. 5 (Tables 4, 5, 7, 8).
+EXTRA_VARIANTS = ("xoroshiro128*", "xoroshiro64*", "xoroshiro64**", "xoshiro512+", "xoshiro512++",
+                  "xoshiro512**", "xoroshiro1024*", "xoroshiro1024++", "xoroshiro1024**")
+ALL_VARIANTS = BULK_VARIANTS + ("xoshiro128+",) + EXTRA_VARIANTS
+# Generators whose states fit the 32-byte slots of batches and servers.
+SLOT_VARIANTS = BULK_VARIANTS + ("xoshiro128+", "xoroshiro128*", "xoroshiro64*", "xoroshiro64**")
 
 # xoshiro256**, SplitMix64(0x0123456789ABCDEF), 1024 streams by successive
 # jumps, 1024 outputs each, as raw uint64 and as doubles.
@@ -35,7 +40,7 @@ CONFIG_JUMPSTART = dict(variant="xoshiro256++", seed=42, kinds=("jump", "long"),
 
 
 def native_dtype(variant: str) -> str:
-    return "u32" if variant.startswith("xoshiro128") else "u64"
+    return "u32" if variant.startswith(("xoshiro128", "xoroshiro64")) else "u64"
 
 
 def sample_indices(S: int, count: int, seed: int) -> np.ndarray:
