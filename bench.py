@@ -50,6 +50,7 @@ def parse_args():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-extra", action="store_true")
+    p.add_argument("--no-analysis", action="store_true")
     p.add_argument("--serve-requests", type=int, default=20000)
     p.add_argument("--batched-steps", type=int, default=5)
     p.add_argument("--profile", choices=["fill", "streams", "batch"], default=None,
@@ -236,6 +237,18 @@ def cpu_baseline(seconds):
             "seconds": t, "bytes": b}
 
 
+def analysis_cpu_baseline():
+    """The oracle on the analysis workloads of run_analysis (same inputs)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    O.zeroland("xoshiro256**", 1000, 4)
+    t1 = time.perf_counter()
+    L = O.linear_complexity("xoshiro256+", 1, ANALYSIS_LC_SMALL[2], 1)
+    t2 = time.perf_counter()
+    return {"kind": "oracle", "cores": 1, "zeroland_ms": (t1 - t0) * 1e3, "lc_small_ms": (t2 - t1) * 1e3,
+            "lc_small_value": L, "sample": "the same two calls as the device, single-threaded plain C"}
+
+
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -403,6 +416,8 @@ def run_xr(args):
         line["serving"] = run_serving(xr, ctx, args)
     if not args.no_extra:
         line["extra_generators"] = run_extra(xr, ctx, args)
+    if not args.no_analysis:
+        line["analysis"] = run_analysis(xr, ctx, args)
     if not args.no_e2e:
         line["e2e"] = run_e2e(ctx, args, first, bytes_per_step, world, dist)
     if dist:
@@ -506,6 +521,50 @@ def run_extra(xr, ctx, args):
             del out
     torch.cuda.synchronize()
     assert ctx.status() == 0
+    return res
+
+
+# Table 13: xoshiro256+ bit 1 (complexity 32896) and xoroshiro128+ bit 2
+# (349632, the largest), each from 2 L + 200 bits of SplitMix64(1).
+ANALYSIS_LC_SMALL = ("xoshiro256+", 1, 2 * 32896 + 200)
+ANALYSIS_LC_LARGE = ("xoroshiro128+", 2, 2 * 349632 + 200)
+
+
+def run_analysis(xr, ctx, args):
+    """The paper's analysis workloads: escaping zeroland (Sec. 8; all one-bit
+    states of xoshiro256**, 1000 outputs, windows of 4) timed with events, and
+    Berlekamp-Massey linear complexity (Sec. 9.3) of two Table 13 rows timed
+    around the blocking call (generation of the bits, the one-CTA
+    Berlekamp-Massey, the 8-byte read back)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ctx.zeroland("xoshiro256**", 1000, 4)
+    ts = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.zeroland("xoshiro256**", 1000, 4)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    res = {"zeroland": {"workload": "xoshiro256**, 256 one-bit states x 1000 outputs, windows of 4",
+                        "ms": statistics.median(ts)}}
+    for key, (v, bit, N) in (("lc_small", ANALYSIS_LC_SMALL), ("lc_large", ANALYSIS_LC_LARGE)):
+        st = ctx.empty_states(v, 1)
+        ctx.seed(v, 1, st)
+        ctx.linear_complexity(v, bit, N, st)
+        ts, L = [], None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            L = ctx.linear_complexity(v, bit, N, st)
+            ts.append(time.perf_counter() - t0)
+        ms = statistics.median(ts) * 1e3
+        res[key] = {"workload": "%s bit %d, %d bits" % (v, bit, N), "value": L, "ms": ms,
+                    "ns_per_bit": ms * 1e6 / N}
+    assert ctx.status() == 0
+    if not args.no_cpu_baseline:
+        res["cpu_baseline"] = analysis_cpu_baseline()
     return res
 
 

@@ -340,6 +340,32 @@ int xr_server_stats(xr_server *s, xr_serve_stats *out);
 int xr_server_replay(xr_server *s, const double *arrival_us, const uint32_t *clients, const uint64_t *ns,
                      const int *dtypes, size_t nreq, double *latency_us, double *wall_us);
 
+/* ---- analysis workloads of the paper ---------------------------------------
+ * Escaping zeroland (Sec. 8): for each of the n states with exactly one bit
+ * set, the first nout outputs are generated; d_counts[t] (device, nout -
+ * window + 1 uint64) receives the number of one bits in outputs t .. t +
+ * window - 1 summed over the n states.  The paper's curve (window 4, 1000
+ * outputs) is d_counts[t] / (n * window * word bits).  window <= 64.
+ * XR_EINVAL on bad sizes. */
+int xr_zeroland(xr_ctx *ctx, int variant, size_t nout, size_t window, uint64_t *d_counts, void *stream);
+
+/* Linear complexity of one output bit (Sec. 9.3, Table 13): Berlekamp-Massey
+ * over F2 on bit `bit` (0 = least significant) of the first N outputs of the
+ * sequence starting at d_state (device, 16-byte aligned, read only, not
+ * advanced).  d_scratch (device, caller-owned, 16-byte aligned) must hold
+ * XR_LC_SCRATCH_BYTES(N) bytes.
+ * Writes the linear complexity of the N-bit prefix to *h_lc and waits for the
+ * device; it is the sequence's linear complexity when N >= 2 L.  XR_EINVAL
+ * for bad arguments or N outside 2 .. XR_LC_MAX_BITS.  A prefix complexity
+ * of 32 (floor(N / 64) + 5) or more (above N / 2 + 127, so not decided by an
+ * N-bit prefix) returns XR_EUNSUPPORTED.  One CTA with its polynomials (and, up to about 740,000
+ * bits, the sequence) in shared memory; calls on different streams run
+ * concurrently. */
+#define XR_LC_MAX_BITS ((size_t)1 << 20)
+#define XR_LC_SCRATCH_BYTES(N) (((((N) + 31) / 32 + 2) * 4 + 15) / 16 * 16 + 16)
+int xr_linear_complexity(xr_ctx *ctx, int variant, int bit, size_t N, const void *d_state, void *d_scratch,
+                         size_t scratch_bytes, uint64_t *h_lc, void *stream);
+
 /* ---- status and inspection ------------------------------------------------ */
 
 /* Sticky device status: XR_OK, or the first error a kernel recorded

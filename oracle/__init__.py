@@ -107,6 +107,7 @@ def _lib():
     lib.orc_state_to_bits.argtypes = [ctypes.c_int, _u64p, _u64p]
     lib.orc_bits_to_state.argtypes = [ctypes.c_int, _u64p, _u64p]
     lib.orc_scramble.argtypes = [ctypes.c_int, _u64p, _u64p]
+    lib.orc_zeroland.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, _u64p]
     return lib
 
 
@@ -439,3 +440,12 @@ def bulk_fill(name: str, kind: str, base: np.ndarray, S: int, m: int, first: int
     out = np.zeros(S * m, np.uint64)
     _lib().orc_bulk_fill(_index(name), _p(coef), n, _p(np.ascontiguousarray(b)), 0, S, m, _p(out))
     return out
+
+
+def zeroland(name: str, nout: int = 1000, window: int = 4) -> np.ndarray:
+    """Sec. 8: counts[t] = one bits in outputs t .. t+window-1, summed over the
+    n states with exactly one bit set; the paper plots counts / (n window w)."""
+    counts = np.zeros(nout - window + 1, np.uint64)
+    if _lib().orc_zeroland(_index(name), nout, window, _p(counts)) != 0:
+        raise ValueError("bad window")
+    return counts

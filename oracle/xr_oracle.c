@@ -752,3 +752,29 @@ int orc_bulk_fill(int gi, const u64 *coef, int ncoef, const u64 *base, size_t fi
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Escaping zeroland (Sec. 8): for each of the n states with exactly one bit */
+/* set, the first nout outputs; counts[t] = number of one bits in outputs    */
+/* t .. t + window - 1, summed over the n states.                            */
+/* ------------------------------------------------------------------------ */
+
+int orc_zeroland(int gi, size_t nout, size_t window, u64 *counts)
+{
+    const gen_t *g = gen(gi);
+    if (!g || window == 0 || window > nout) return -1;
+    const int n = g->k * g->w;
+    const size_t T = nout - window + 1;
+    memset(counts, 0, sizeof(u64) * T);
+    u64 *ones = (u64 *)malloc(sizeof(u64) * nout);
+    if (!ones) return -1;
+    for (int j = 0; j < n; j++) {
+        u64 s[16] = {0};
+        s[j / g->w] = 1ull << (j % g->w);
+        for (size_t i = 0; i < nout; i++) ones[i] = (u64)__builtin_popcountll(next_output(g, s));
+        for (size_t t = 0; t < T; t++)
+            for (size_t i = t; i < t + window; i++) counts[t] += ones[i];
+    }
+    free(ones);
+    return 0;
+}

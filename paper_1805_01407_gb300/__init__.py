@@ -129,6 +129,10 @@ def lib():
         L.xr_server_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
         L.xr_server_replay.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(i), sz, dp, dp]
+        L.xr_zeroland.argtypes = [vp, i, sz, sz, vp, vp]
+        L.xr_zeroland.restype = i
+        L.xr_linear_complexity.argtypes = [vp, i, i, sz, vp, vp, sz, ctypes.POINTER(ctypes.c_uint64), vp]
+        L.xr_linear_complexity.restype = i
         for fn in ("xr_server_create", "xr_server_destroy", "xr_server_submit", "xr_server_wait",
                    "xr_server_release", "xr_server_read", "xr_server_client_state", "xr_server_stats",
                    "xr_server_replay"):
@@ -333,6 +337,27 @@ class Context:
         buf = ctypes.create_string_buffer(b, len(b))
         _check(lib().xr_fill_host(self._h, _v(variant), KINDS[kind], buf, first, S, m, DTYPES[dtype],
                                   h_out.data_ptr(), _stream(stream)), "xr_fill_host")
+
+    def zeroland(self, variant, nout=1000, window=4, stream=None):
+        """Sec. 8 escaping-zeroland counts (a CUDA int64 tensor of nout-window+1
+        entries, one bits per window summed over all one-bit states)."""
+        import torch
+        out = torch.empty(nout - window + 1, dtype=torch.int64, device=self.device)
+        _check(lib().xr_zeroland(self._h, _v(variant), nout, window, out.data_ptr(), _stream(stream)),
+               "xr_zeroland")
+        return out
+
+    def linear_complexity(self, variant, bit, N, d_state, stream=None):
+        """Sec. 9.3 linear complexity (Berlekamp-Massey over F2) of bit `bit`
+        of the first N outputs from the state in d_state (not advanced)."""
+        import torch
+        _need(d_state, state_bytes(variant), "d_state")
+        nbytes = ((((N + 31) // 32 + 2) * 4 + 15) // 16) * 16 + 16
+        scratch = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        L = ctypes.c_uint64(0)
+        _check(lib().xr_linear_complexity(self._h, _v(variant), bit, N, d_state.data_ptr(), scratch.data_ptr(),
+                                          nbytes, ctypes.byref(L), _stream(stream)), "xr_linear_complexity")
+        return L.value
 
     def status(self, reset=False):
         return lib().xr_status(self._h, int(bool(reset)))

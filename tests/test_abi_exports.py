@@ -66,6 +66,10 @@ def test_argument_checks_need_no_device(libxr):
     assert libxr.xr_seed(None, 0, 1, vp(16), None) == xr.XR_EINVAL
     assert libxr.xr_status(None, 0) == xr.XR_EINVAL
     assert libxr.xr_ctx_create(0, None) == xr.XR_EINVAL
+    L = ctypes.c_uint64(0)
+    assert libxr.xr_zeroland(None, 0, 1000, 4, vp(16), None) == xr.XR_EINVAL
+    assert libxr.xr_linear_complexity(None, 0, 0, 100, vp(16), vp(16), 1 << 12, ctypes.byref(L), None) \
+        == xr.XR_EINVAL
 
 
 def test_context_creation_fails_cleanly_without_gpu(libxr):

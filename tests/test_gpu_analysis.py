@@ -1,0 +1,111 @@
+"""The paper's analysis workloads on the device, against the oracle and the
+paper: escaping zeroland (Sec. 8) and the linear complexity of single output
+bits by Berlekamp-Massey (Sec. 9.3, Table 13).  Integer results: bit-exact."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xr():
+    from paper_1805_01407_gb300 import build
+    build.build()
+    import paper_1805_01407_gb300 as xr
+    return xr
+
+
+@pytest.fixture(scope="module")
+def ctx(xr):
+    c = xr.Context(0)
+    yield c
+    c.close()
+
+
+# ------------------------------------------------------------------ zeroland
+
+@pytest.mark.parametrize("name", W.ALL_VARIANTS)
+def test_zeroland_equals_oracle(ctx, name):
+    """The paper's setting: 1000 outputs, windows of 4."""
+    got = ctx.zeroland(name, 1000, 4).cpu().numpy().astype(np.uint64)
+    assert (got == O.zeroland(name, 1000, 4)).all()
+
+
+@pytest.mark.parametrize("name,nout,window", [("xoshiro256**", 1, 1), ("xoroshiro128+", 64, 64),
+                                              ("xoshiro128**", 5000, 1), ("xoroshiro64*", 300, 63),
+                                              ("xoroshiro1024++", 130, 7), ("xoshiro512+", 2, 2)])
+def test_zeroland_window_edges(ctx, name, nout, window):
+    got = ctx.zeroland(name, nout, window).cpu().numpy().astype(np.uint64)
+    assert (got == O.zeroland(name, nout, window)).all()
+
+
+def test_zeroland_first_output_closed_form(ctx):
+    """One bits of the first output over the one-bit states (derived by hand
+    from the scramblers' definitions; the same numbers pin the oracle)."""
+    want = {"xoroshiro128+": 128, "xoshiro256++": 192, "xoshiro256**": 246, "xoroshiro128**": 246,
+            "xoshiro128**": 118, "xoshiro128++": 96}
+    for name, v in want.items():
+        assert int(ctx.zeroland(name, 3, 1)[0]) == v, name
+
+
+def test_zeroland_rejects_bad_windows(ctx, xr):
+    for nout, window in ((10, 0), (100, 65), (3, 4)):
+        with pytest.raises(xr.XRError):
+            ctx.zeroland("xoshiro256**", nout, window)
+
+
+# ------------------------------------------------------------------ linear complexity
+
+def seeded(ctx, name, seed):
+    st = ctx.empty_states(name, 1)
+    ctx.seed(name, seed, st)
+    return st
+
+
+def _table13(golden):
+    rows = [(g, int(b), int(lc)) for g, b, lc in golden("plus_linear_complexity.txt")]
+    return [r for r in rows if not r[0].startswith("engine/")]
+
+
+def test_linear_complexity_table13(ctx, golden):
+    """Every generator row of Table 13 (the lowest bits of the + generators),
+    computed on the device from 2 L + 200 bits."""
+    for g, b, lc in _table13(golden):
+        assert ctx.linear_complexity(g, b, 2 * lc + 200, seeded(ctx, g, 1)) == lc, (g, b)
+
+
+@pytest.mark.parametrize("name,bit,N", [("xoshiro256**", 63, 20000), ("xoshiro256++", 0, 6000),
+                                        ("xoroshiro128**", 5, 9001), ("xoroshiro128++", 40, 4097),
+                                        ("xoshiro128**", 31, 8000), ("xoroshiro64**", 3, 3333),
+                                        ("xoshiro512**", 17, 5000), ("xoroshiro1024++", 62, 7000),
+                                        ("xoroshiro128+", 3, 70000), ("xoroshiro128*", 60, 12345)])
+def test_linear_complexity_equals_oracle(ctx, name, bit, N):
+    """Nonlinear bits (complexity close to N / 2) and a Table 13 bit whose
+    complexity exceeds what N bits decide."""
+    for seed in (1, 99):
+        assert ctx.linear_complexity(name, bit, N, seeded(ctx, name, seed)) == \
+            O.linear_complexity(name, bit, N, seed), (name, bit, N, seed)
+
+
+@pytest.mark.parametrize("N", [2, 3, 31, 32, 33, 63, 64, 65, 127, 1000, 1025])
+def test_linear_complexity_short_prefixes(ctx, N):
+    for name, bit in (("xoshiro256+", 0), ("xoshiro256**", 40), ("xoshiro128++", 7)):
+        assert ctx.linear_complexity(name, bit, N, seeded(ctx, name, 5)) == \
+            O.linear_complexity(name, bit, N, 5), (name, bit, N)
+
+
+def test_linear_complexity_leaves_the_state(ctx):
+    st = seeded(ctx, "xoshiro256+", 3)
+    before = st.clone()
+    ctx.linear_complexity("xoshiro256+", 1, 1000, st)
+    assert bool((st == before).all())
+
+
+def test_linear_complexity_rejects_bad_args(ctx, xr):
+    st = seeded(ctx, "xoshiro128+", 1)
+    for bit, N in ((32, 100), (-1, 100), (0, 1), (0, (1 << 20) + 1)):
+        with pytest.raises(xr.XRError):
+            ctx.linear_complexity("xoshiro128+", bit, N, st)

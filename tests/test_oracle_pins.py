@@ -469,3 +469,49 @@ def test_bulk_fill_equals_streams_then_fill():
     b = O.bulk_fill(name, "jump", base, 33, 17)
     assert (a == b).all()
     assert (st[0] == base).all()
+
+
+# --------------------------------------------------------------- P9: escaping zeroland (Sec. 8)
+
+# One bits of the first output, summed over the n states with one bit set.
+# Derived by hand from the scramblers' definitions (Sec. 4):
+#   +  : the sum of two words of which at most one is nonzero has one bit for
+#        the states with the bit in a summed word, none otherwise;
+#   ++ : rotl(a + b, r) + a has 2 bits for a bit in a (distinct positions, no
+#        carry), 1 for a bit in b;
+#   ** : rotl(5 s, 7) * 9.  5 * 2^b has bits b, b + 2 (one bit when b + 2 >= w);
+#        * 9 adds those bits shifted by 3 and never carries (the two pairs
+#        cannot overlap), dropping the shifted bits that reach w.  For w = 64
+#        that gives 62 * 2 + 59 + 59 + 2 + 2 = 246, for w = 32 30 * 2 + 27 + 27
+#        + 2 + 2 = 118.
+ZEROLAND_FIRST_OUTPUT = {
+    "xoroshiro128+": 128, "xoshiro256+": 128, "xoshiro128+": 64,
+    "xoshiro256++": 192, "xoroshiro128++": 192, "xoshiro128++": 96,
+    "xoshiro256**": 246, "xoroshiro128**": 246, "xoshiro128**": 118,
+}
+
+
+@pytest.mark.parametrize("name", sorted(ZEROLAND_FIRST_OUTPUT))
+def test_zeroland_first_output_closed_form(name):
+    assert int(O.zeroland(name, 3, 1)[0]) == ZEROLAND_FIRST_OUTPUT[name]
+
+
+def test_zeroland_windows_add_up():
+    """A window's count is the sum of the single-output counts it covers."""
+    for name in ("xoshiro256++", "xoroshiro64**", "xoshiro512**"):
+        one = O.zeroland(name, 300, 1).astype(np.int64)
+        for window in (2, 4, 17, 64):
+            w = O.zeroland(name, 300, window).astype(np.int64)
+            want = np.convolve(one, np.ones(window, np.int64), mode="valid")
+            assert (w == want).all(), (name, window)
+
+
+@pytest.mark.parametrize("name", ["xoshiro256**", "xoroshiro128+", "xoshiro128++", "xoroshiro1024*"])
+def test_zeroland_escapes_to_one_half(name):
+    """Sec. 8: starting near the zero state the outputs hold few ones; after a
+    number of steps depending on the engine's diffusion they look random (one
+    half ones).  The last 200 windows of 1000 outputs are within 0.02 of 1/2."""
+    n, w, window = O.state_bits(name), O.word_bits(name), 4
+    ratio = O.zeroland(name, 1000, window) / float(n * window * w)
+    assert ratio[0] < 0.2
+    assert abs(ratio[-200:].mean() - 0.5) < 0.02
