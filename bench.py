@@ -53,7 +53,7 @@ def parse_args():
     p.add_argument("--no-analysis", action="store_true")
     p.add_argument("--serve-requests", type=int, default=20000)
     p.add_argument("--batched-steps", type=int, default=5)
-    p.add_argument("--profile", choices=["fill", "streams", "batch"], default=None,
+    p.add_argument("--profile", choices=["fill", "streams", "batch", "lc", "lc-bulk"], default=None,
                    help="run a small case for an ncu capture instead of the benchmark")
     p.add_argument("--profile-variant", default="xoshiro256**")
     p.add_argument("--profile-dtype", default=None)
@@ -245,8 +245,17 @@ def analysis_cpu_baseline():
     t1 = time.perf_counter()
     L = O.linear_complexity("xoshiro256+", 1, ANALYSIS_LC_SMALL[2], 1)
     t2 = time.perf_counter()
+    c = W.CONFIG_LC_BULK
+    jobs = W.lc_bulk_jobs(**c)
+    sample = jobs[::56]
+    for v, b, N in sample:
+        O.linear_complexity(v, b, N, c["seed"])
+    t3 = time.perf_counter()
+    per_job = (t3 - t2) / len(sample)
     return {"kind": "oracle", "cores": 1, "zeroland_ms": (t1 - t0) * 1e3, "lc_small_ms": (t2 - t1) * 1e3,
-            "lc_small_value": L, "sample": "the same two calls as the device, single-threaded plain C"}
+            "lc_small_value": L, "lc_bulk_ms_estimate": per_job * len(jobs) * 1e3,
+            "sample": "zeroland and lc_small: the same calls as the device; lc_bulk: %d of the %d sequences "
+                      "(every 56th), scaled to all; single-threaded plain C" % (len(sample), len(jobs))}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -562,6 +571,25 @@ def run_analysis(xr, ctx, args):
         ms = statistics.median(ts) * 1e3
         res[key] = {"workload": "%s bit %d, %d bits" % (v, bit, N), "value": L, "ms": ms,
                     "ns_per_bit": ms * 1e6 / N}
+    c = W.CONFIG_LC_BULK
+    jobs = W.lc_bulk_jobs(**c)
+    states = torch.zeros(len(jobs) * 128, dtype=torch.uint8, device="cuda")
+    for j, (v, _, _) in enumerate(jobs):
+        ctx.seed(v, c["seed"], states[j * 128:])
+    ctx.linear_complexity_many(jobs, states)
+    ts = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got = ctx.linear_complexity_many(jobs, states)
+        ts.append(time.perf_counter() - t0)
+    ms = statistics.median(ts) * 1e3
+    res["lc_bulk"] = {"workload": "every bit of the 8 bulk generators, %d sequences x %d bits, SplitMix64(%d)"
+                                  % (len(jobs), c["N"], c["seed"]),
+                      "jobs": len(jobs), "ms": ms, "jobs_per_s": len(jobs) / (ms / 1e3),
+                      "bits_per_s": len(jobs) * c["N"] / (ms / 1e3),
+                      "lowest_bits": {v: got[[k for k, (vv, b, _) in enumerate(jobs) if vv == v][0]]
+                                      for v in c["variants"]}}
     assert ctx.status() == 0
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = analysis_cpu_baseline()
@@ -648,6 +676,8 @@ def run_profile(args):
     libbuild.build()
     if args.profile == "batch":
         return run_profile_batch(args)
+    if args.profile in ("lc", "lc-bulk"):
+        return run_profile_lc(args)
     v = args.profile_variant
     d = args.profile_dtype or W.native_dtype(v)
     S, m = args.profile_streams, W.CONFIG_BULK["m"]
@@ -665,6 +695,34 @@ def run_profile(args):
         torch.cuda.synchronize()
         assert ctx.status() == 0
     print("profile case done: %s %s S=%d m=%d" % (args.profile, v, S, m))
+    return 0
+
+
+def run_profile_lc(args):
+    """Linear complexity for ncu: lc = the largest Table 13 row (one CTA),
+    lc-bulk = the bulk configuration (448 CTAs); one warm-up call, then
+    --profile-launches calls."""
+    import torch
+    import paper_1805_01407_gb300 as xr
+    with xr.Context(0) as ctx:
+        if args.profile == "lc":
+            v, bit, N = ANALYSIS_LC_LARGE
+            st = ctx.empty_states(v, 1)
+            ctx.seed(v, 1, st)
+            for _ in range(1 + args.profile_launches):
+                L = ctx.linear_complexity(v, bit, N, st)
+            what = "%s bit %d, %d bits: %d" % (v, bit, N, L)
+        else:
+            c = W.CONFIG_LC_BULK
+            jobs = W.lc_bulk_jobs(**c)
+            states = torch.zeros(len(jobs) * 128, dtype=torch.uint8, device="cuda")
+            for j, (v, _, _) in enumerate(jobs):
+                ctx.seed(v, c["seed"], states[j * 128:])
+            for _ in range(1 + args.profile_launches):
+                ctx.linear_complexity_many(jobs, states)
+            what = "%d sequences x %d bits" % (len(jobs), c["N"])
+        assert ctx.status() == 0
+    print("profile case done: %s" % what)
     return 0
 
 

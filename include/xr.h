@@ -353,18 +353,35 @@ int xr_zeroland(xr_ctx *ctx, int variant, size_t nout, size_t window, uint64_t *
  * over F2 on bit `bit` (0 = least significant) of the first N outputs of the
  * sequence starting at d_state (device, 16-byte aligned, read only, not
  * advanced).  d_scratch (device, caller-owned, 16-byte aligned) must hold
- * XR_LC_SCRATCH_BYTES(N) bytes.
- * Writes the linear complexity of the N-bit prefix to *h_lc and waits for the
- * device; it is the sequence's linear complexity when N >= 2 L.  XR_EINVAL
- * for bad arguments or N outside 2 .. XR_LC_MAX_BITS.  A prefix complexity
- * of 32 (floor(N / 64) + 5) or more (above N / 2 + 127, so not decided by an
- * N-bit prefix) returns XR_EUNSUPPORTED.  One CTA with its polynomials (and, up to about 740,000
- * bits, the sequence) in shared memory; calls on different streams run
- * concurrently. */
-#define XR_LC_MAX_BITS ((size_t)1 << 20)
-#define XR_LC_SCRATCH_BYTES(N) (((((N) + 31) / 32 + 2) * 4 + 15) / 16 * 16 + 16)
+ * XR_LC_SCRATCH_BYTES(N) bytes.  Writes the linear complexity of the N-bit
+ * prefix to *h_lc and waits for the device; it is the sequence's linear
+ * complexity when N >= 2 L.  XR_EINVAL for bad arguments or N outside
+ * 2 .. XR_LC_MAX_BITS.  A prefix complexity of 32 (floor(N / 64) + 5) or more
+ * (above N / 2 + 127, so not decided by an N-bit prefix) returns
+ * XR_EUNSUPPORTED.  One CTA with every polynomial and the sequence window in
+ * registers; calls on different streams run concurrently. */
+#define XR_LC_MAX_BITS ((size_t)786000)
+#define XR_LC_SCRATCH_BYTES(N) (64 + ((((N) + 31) / 32 + 22) * 4 + 15) / 16 * 16)
 int xr_linear_complexity(xr_ctx *ctx, int variant, int bit, size_t N, const void *d_state, void *d_scratch,
                          size_t scratch_bytes, uint64_t *h_lc, void *stream);
+
+/* Many linear complexities in one call: job j takes the state at d_states +
+ * j * state_stride (device, 16-byte aligned; the stride a multiple of 16 and
+ * at least the largest state) and gives h_lc[j] (host): the complexity, or
+ * UINT64_MAX where xr_linear_complexity would return XR_EUNSUPPORTED.  One CTA
+ * per job, so up to a few hundred jobs run at once.  d_scratch (device,
+ * 16-byte aligned) must hold xr_lc_scratch_bytes(jobs, njobs) bytes.  Any bad
+ * job makes the call return XR_EINVAL before work is enqueued.  Waits for the
+ * device. */
+typedef struct xr_lc_job {
+    int32_t variant;
+    int32_t bit;
+    uint64_t N;
+} xr_lc_job;
+size_t xr_lc_scratch_bytes(const xr_lc_job *jobs, size_t njobs);
+int xr_linear_complexity_many(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, const void *d_states,
+                              size_t state_stride, void *d_scratch, size_t scratch_bytes, uint64_t *h_lc,
+                              void *stream);
 
 /* ---- status and inspection ------------------------------------------------ */
 

@@ -35,6 +35,7 @@ LAYOUTS = {"stream": 0, "interleaved": 1}
 KINDS = {"jump": 0, "long": 1}
 
 XR_OK, XR_EINVAL, XR_EZERO_STATE, XR_ENOMEM, XR_ECUDA, XR_ETIMEOUT, XR_EUNSUPPORTED = range(7)
+XR_LC_MAX_BITS = 786000  # longest prefix xr_linear_complexity accepts
 
 _lib = None
 
@@ -56,6 +57,11 @@ class Request(ctypes.Structure):
     """xr_request of include/xr.h."""
     _fields_ = [("variant", ctypes.c_int), ("dtype", ctypes.c_int), ("n", ctypes.c_uint64),
                 ("slot", ctypes.c_uint64), ("out_offset", ctypes.c_uint64)]
+
+
+class LcJob(ctypes.Structure):
+    """xr_lc_job of include/xr.h."""
+    _fields_ = [("variant", ctypes.c_int32), ("bit", ctypes.c_int32), ("N", ctypes.c_uint64)]
 
 
 class XRError(RuntimeError):
@@ -133,6 +139,11 @@ def lib():
         L.xr_zeroland.restype = i
         L.xr_linear_complexity.argtypes = [vp, i, i, sz, vp, vp, sz, ctypes.POINTER(ctypes.c_uint64), vp]
         L.xr_linear_complexity.restype = i
+        L.xr_lc_scratch_bytes.argtypes = [ctypes.POINTER(LcJob), sz]
+        L.xr_lc_scratch_bytes.restype = sz
+        L.xr_linear_complexity_many.argtypes = [vp, ctypes.POINTER(LcJob), sz, vp, sz, vp, sz,
+                                                ctypes.POINTER(ctypes.c_uint64), vp]
+        L.xr_linear_complexity_many.restype = i
         for fn in ("xr_server_create", "xr_server_destroy", "xr_server_submit", "xr_server_wait",
                    "xr_server_release", "xr_server_read", "xr_server_client_state", "xr_server_stats",
                    "xr_server_replay"):
@@ -352,12 +363,28 @@ class Context:
         of the first N outputs from the state in d_state (not advanced)."""
         import torch
         _need(d_state, state_bytes(variant), "d_state")
-        nbytes = ((((N + 31) // 32 + 2) * 4 + 15) // 16) * 16 + 16
-        scratch = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        job = LcJob(_v(variant), bit, N)
+        nbytes = lib().xr_lc_scratch_bytes(ctypes.byref(job), 1)
+        scratch = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=self.device)
         L = ctypes.c_uint64(0)
         _check(lib().xr_linear_complexity(self._h, _v(variant), bit, N, d_state.data_ptr(), scratch.data_ptr(),
                                           nbytes, ctypes.byref(L), _stream(stream)), "xr_linear_complexity")
         return L.value
+
+    def linear_complexity_many(self, jobs, d_states, state_stride=128, stream=None):
+        """Linear complexities of many (variant, bit, N) jobs in one call; job
+        j reads its state at byte j * state_stride of d_states.  Returns a list
+        of ints, None where N bits cannot decide the complexity."""
+        import torch
+        arr = (LcJob * max(len(jobs), 1))(*[LcJob(_v(v), b, n) for (v, b, n) in jobs])
+        _need(d_states, (len(jobs) - 1) * state_stride + 16 if jobs else 0, "d_states")
+        nbytes = lib().xr_lc_scratch_bytes(arr, len(jobs))
+        scratch = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=self.device)
+        out = (ctypes.c_uint64 * max(len(jobs), 1))()
+        _check(lib().xr_linear_complexity_many(self._h, arr, len(jobs), d_states.data_ptr(), state_stride,
+                                               scratch.data_ptr(), nbytes, out, _stream(stream)),
+               "xr_linear_complexity_many")
+        return [None if out[j] == 2**64 - 1 else int(out[j]) for j in range(len(jobs))]
 
     def status(self, reset=False):
         return lib().xr_status(self._h, int(bool(reset)))

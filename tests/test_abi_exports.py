@@ -31,6 +31,26 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_binding_constants_match_the_header():
+    import paper_1805_01407_gb300 as xr
+    text = open(os.path.join(ROOT, "include", "xr.h")).read()
+    assert int(re.search(r"#define XR_LC_MAX_BITS \(\(size_t\)(\d+)\)", text).group(1)) == xr.XR_LC_MAX_BITS
+    assert int(re.search(r"XR_NUM_VARIANTS\s*=\s*(\d+)", text).group(1)) == len(xr.VARIANTS)
+
+
+def test_lc_scratch_macro_matches_the_library(libxr):
+    """XR_LC_SCRATCH_BYTES(N) (header) is what xr_lc_scratch_bytes gives for one job."""
+    import paper_1805_01407_gb300 as xr
+    text = open(os.path.join(ROOT, "include", "xr.h")).read()
+    expr = re.search(r"#define XR_LC_SCRATCH_BYTES\(N\) (.+)", text).group(1).replace("/", "//")
+    for N in (2, 31, 32, 33, 1000, 65992, 699464, 786000):
+        job = xr.LcJob(0, 0, N)
+        assert libxr.xr_lc_scratch_bytes(ctypes.byref(job), 1) == eval(expr.replace("(N)", "(%d)" % N))
+    jobs = (xr.LcJob * 3)(xr.LcJob(0, 0, 100), xr.LcJob(3, 1, 5000), xr.LcJob(7, 2, 77))
+    one = [libxr.xr_lc_scratch_bytes(ctypes.byref(jobs[k]), 1) for k in range(3)]
+    assert libxr.xr_lc_scratch_bytes(jobs, 3) > max(one)
+
+
 def test_every_declared_symbol_is_exported(libxr):
     for name in header_functions():
         assert hasattr(libxr, name), name
@@ -70,6 +90,9 @@ def test_argument_checks_need_no_device(libxr):
     assert libxr.xr_zeroland(None, 0, 1000, 4, vp(16), None) == xr.XR_EINVAL
     assert libxr.xr_linear_complexity(None, 0, 0, 100, vp(16), vp(16), 1 << 12, ctypes.byref(L), None) \
         == xr.XR_EINVAL
+    job = xr.LcJob(0, 0, 100)
+    assert libxr.xr_linear_complexity_many(None, ctypes.byref(job), 1, vp(16), 128, vp(16), 1 << 12,
+                                           ctypes.byref(L), None) == xr.XR_EINVAL
 
 
 def test_context_creation_fails_cleanly_without_gpu(libxr):

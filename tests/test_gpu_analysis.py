@@ -90,6 +90,15 @@ def test_linear_complexity_equals_oracle(ctx, name, bit, N):
             O.linear_complexity(name, bit, N, seed), (name, bit, N, seed)
 
 
+@pytest.mark.parametrize("name,bit,N", [("xoroshiro128+", 1, 200000), ("xoshiro256+", 0, 600001),
+                                        ("xoroshiro128+", 1, 780000), ("xoshiro256+", 1, 786000)])
+def test_linear_complexity_long_prefixes(ctx, xr, name, bit, N):
+    """Long prefixes of low-complexity bits (4, 8 and 12 polynomial words per
+    thread, up to the largest prefix accepted)."""
+    assert N <= xr.XR_LC_MAX_BITS
+    assert ctx.linear_complexity(name, bit, N, seeded(ctx, name, 7)) == O.linear_complexity(name, bit, N, 7)
+
+
 @pytest.mark.parametrize("N", [2, 3, 31, 32, 33, 63, 64, 65, 127, 1000, 1025])
 def test_linear_complexity_short_prefixes(ctx, N):
     for name, bit in (("xoshiro256+", 0), ("xoshiro256**", 40), ("xoshiro128++", 7)):
@@ -106,6 +115,70 @@ def test_linear_complexity_leaves_the_state(ctx):
 
 def test_linear_complexity_rejects_bad_args(ctx, xr):
     st = seeded(ctx, "xoshiro128+", 1)
-    for bit, N in ((32, 100), (-1, 100), (0, 1), (0, (1 << 20) + 1)):
+    for bit, N in ((32, 100), (-1, 100), (0, 1), (0, xr.XR_LC_MAX_BITS + 1)):
         with pytest.raises(xr.XRError):
             ctx.linear_complexity("xoshiro128+", bit, N, st)
+
+
+# ------------------------------------------------------------------ many at once
+
+def states_for(ctx, xr, jobs, seeds):
+    import torch
+    st = torch.zeros(len(jobs) * 128, dtype=torch.uint8, device="cuda")
+    for j, ((v, _, _), sd) in enumerate(zip(jobs, seeds)):
+        ctx.seed(v, sd, st[j * 128:])
+    return st
+
+
+def test_linear_complexity_many_table13(ctx, xr, golden):
+    """All generator rows of Table 13 in one call."""
+    rows = _table13(golden)
+    jobs = [(g, b, 2 * lc + 200) for g, b, lc in rows]
+    got = ctx.linear_complexity_many(jobs, states_for(ctx, xr, jobs, [1] * len(jobs)))
+    assert got == [lc for _, _, lc in rows]
+
+
+def test_linear_complexity_many_equals_oracle(ctx, xr):
+    """A mixed batch (every generator, low and high bits, prefixes from 2 to
+    40000 bits, repeated jobs) against the oracle job by job, and against the
+    single call."""
+    rng = np.random.default_rng(11)
+    jobs, seeds = [], []
+    for j in range(60):
+        v = W.ALL_VARIANTS[j % len(W.ALL_VARIANTS)]
+        bit = int(rng.integers(0, O.word_bits(v)))
+        N = int(np.exp(rng.uniform(np.log(2), np.log(40000))))
+        jobs.append((v, bit, N))
+        seeds.append(int(rng.integers(1, 1 << 40)))
+    jobs += jobs[:3]
+    seeds += seeds[:3]
+    got = ctx.linear_complexity_many(jobs, states_for(ctx, xr, jobs, seeds))
+    for (v, bit, N), sd, L in zip(jobs, seeds, got):
+        assert L == O.linear_complexity(v, bit, N, sd), (v, bit, N, sd)
+    for k in (0, 7, 31):
+        v, bit, N = jobs[k]
+        assert ctx.linear_complexity(v, bit, N, seeded(ctx, v, seeds[k])) == got[k]
+
+
+def test_linear_complexity_many_rejects_a_bad_job(ctx, xr):
+    import torch
+    st = torch.zeros(3 * 128, dtype=torch.uint8, device="cuda")
+    with pytest.raises(xr.XRError):
+        ctx.linear_complexity_many([("xoshiro256+", 0, 100), ("xoshiro128+", 40, 100), ("xoshiro256+", 1, 100)], st)
+    assert ctx.linear_complexity_many([], st) == []
+
+
+def test_linear_complexity_bulk_configuration_sampled(ctx, xr):
+    """The bulk configuration (every bit of the 8 bulk generators, 2^16 bits):
+    all 448 sequences in one call, every 8th against the oracle; bit 0 of the
+    + generators has the complexity of Table 13 (n)."""
+    c = W.CONFIG_LC_BULK
+    jobs = W.lc_bulk_jobs(**c)
+    got = ctx.linear_complexity_many(jobs, states_for(ctx, xr, jobs, [c["seed"]] * len(jobs)))
+    for k in range(0, len(jobs), 8):
+        v, b, N = jobs[k]
+        assert got[k] == O.linear_complexity(v, b, N, c["seed"]), jobs[k]
+    for k, (v, b, N) in enumerate(jobs):
+        if b == 0 and v.endswith("+") and not v.endswith("++"):
+            assert got[k] == O.state_bits(v), v
+        assert got[k] is not None and 0 < got[k] <= N // 2 + 64

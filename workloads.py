@@ -112,3 +112,15 @@ def serve_trace(nreq, nclients=256, rate=20000.0, min_len=1 << 10, max_len=1 << 
     n = np.clip(n, min_len, max_len)
     dtype = np.where(rng.integers(0, 2, size=nreq) == 0, "u64", "f64")
     return arrival, client, n, list(dtype)
+
+
+# Bulk linear complexity (Sec. 9.3): every output bit of the 8 bulk
+# generators (64 or 32 bits each, 448 sequences), the first 2^16 outputs
+# from SplitMix64(1).  Low bits of the + generators have the small
+# complexities of Table 13; the others come out near N / 2.
+CONFIG_LC_BULK = dict(variants=BULK_VARIANTS, N=1 << 16, seed=1)
+
+
+def lc_bulk_jobs(variants=BULK_VARIANTS, N=1 << 16, **_):
+    """[(variant, bit, N)] for the bulk linear-complexity configuration."""
+    return [(v, b, N) for v in variants for b in range(32 if native_dtype(v) == "u32" else 64)]
