@@ -516,7 +516,8 @@ def run_extra(xr, ctx, args):
         ctx.make_streams(v, "jump", base, 0, S, states)
         for d in (W.native_dtype(v), "f64"):
             out = ctx.empty_output(S * m, d)
-            ctx.fill(v, states, S, m, d, out)
+            for _ in range(3):  # warm-up (the first job follows the serving leg)
+                ctx.fill(v, states, S, m, d, out)
             ts = []
             for _ in range(5):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -660,10 +661,35 @@ def run_e2e(ctx, args, first, bytes_per_step, world, dist):
     el = time.perf_counter() - t0
     el = max_over_ranks(el, dist, "cuda")
     h2d = sum(len(host_base[v]) for v, _ in jobs())
-    return {"value": world * bytes_per_step * args.e2e_steps / el / 1e9, "unit": UNIT,
+    value = world * bytes_per_step * args.e2e_steps / el / 1e9
+    link = d2h_link_gbs(h_out)
+    return {"value": value, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": bytes_per_step,
             "steps": args.e2e_steps, "ms_per_step": 1e3 * el / args.e2e_steps,
-            "api": "xr_fill_host (pinned host output, two staging buffers, copy/compute overlap)"}
+            "api": "xr_fill_host (pinned host output, two staging buffers, copy/compute overlap)",
+            "bound": {"d2h_link_gbs": link, "frac": value / world / link,
+                      "what": "device-to-pinned-host copy bandwidth of this GPU, 1 GiB copies timed with events"}}
+
+
+def d2h_link_gbs(h_out):
+    """The bound of any end-to-end number here: plain device-to-host copies of
+    1 GiB into the same pinned buffer, median of 5, events on the stream."""
+    import torch
+    nb = min(1 << 30, h_out.numel())
+    src = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    src.fill_(1)
+    stream = torch.cuda.current_stream()
+    h_out[:nb].copy_(src, non_blocking=True)
+    ts = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h_out[:nb].copy_(src, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    del src
+    return nb / (statistics.median(ts) / 1e3) / 1e9
 
 
 def run_profile(args):
