@@ -51,6 +51,7 @@ def parse_args():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-extra", action="store_true")
     p.add_argument("--no-analysis", action="store_true")
+    p.add_argument("--no-jumpstart", action="store_true")
     p.add_argument("--serve-requests", type=int, default=20000)
     p.add_argument("--batched-steps", type=int, default=5)
     p.add_argument("--profile", choices=["fill", "streams", "batch", "lc", "lc-bulk"], default=None,
@@ -425,6 +426,8 @@ def run_xr(args):
         line["serving"] = run_serving(xr, ctx, args)
     if not args.no_extra:
         line["extra_generators"] = run_extra(xr, ctx, args)
+    if not args.no_jumpstart:
+        line["jumpstart"] = run_jumpstart(xr, ctx, args)
     if not args.no_analysis:
         line["analysis"] = run_analysis(xr, ctx, args)
     if not args.no_e2e:
@@ -594,6 +597,45 @@ def run_analysis(xr, ctx, args):
     assert ctx.status() == 0
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = analysis_cpu_baseline()
+    return res
+
+
+def run_jumpstart(xr, ctx, args):
+    """Jump-start at scale: 2^24 xoshiro256++ streams J^i(s0) and L^i(s0) from
+    SplitMix64(42), then 64 u64 outputs each; stream starts and fill timed
+    with events on their stream (median of 3).  A stream start is one 256 x
+    256 F2 matrix-vector product (three power-set levels)."""
+    import torch
+    c = W.CONFIG_JUMPSTART
+    v, S, m = c["variant"], c["S"], c["m"]
+    stream = torch.cuda.current_stream()
+    base = ctx.empty_states(v, 1)
+    ctx.seed(v, c["seed"], base)
+    states = ctx.empty_states(v, S)
+    out = ctx.empty_output(S * m, "u64")
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    res = {"workload": "%s, %d streams x %d u64 outputs, SplitMix64(%d) base" % (v, S, m, c["seed"])}
+    for kind in c["kinds"]:
+        ms_streams = timed(lambda: ctx.make_streams(v, kind, base, 0, S, states))
+        ms_fill = timed(lambda: ctx.fill(v, states, S, m, "u64", out))
+        res[kind] = {"streams_ms": ms_streams, "streams_per_s": S / (ms_streams / 1e3),
+                     "fill_ms": ms_fill, "fill_gbs": S * m * 8 / (ms_fill / 1e3) / 1e9,
+                     "total_gbs": S * m * 8 / ((ms_streams + ms_fill) / 1e3) / 1e9}
+    del out, states
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
     return res
 
 

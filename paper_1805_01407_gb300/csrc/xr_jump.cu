@@ -343,29 +343,93 @@ cudaError_t launch_build_power_sets(int engine, const uint32_t *tables, const in
     return err;
 }
 
+// Four-Russians tables of one F2 matrix (n columns of NW words): for each
+// group of three consecutive columns 3g .. 3g+2, the XOR of every subset (8
+// entries), so a matrix-vector product is n/3 table reads instead of n
+// masked XORs.  An entry is split into 16-byte pieces (8-byte for NW = 2);
+// piece h of the 8 entries of a group is stored contiguously (128 or 64
+// bytes), so any lanes of a quarter-warp (half-warp) reading entries of one
+// group hit distinct banks.
+template <int NW>
+struct Russians {
+    static constexpr int n = NW * 32;
+    static constexpr int G = (n + 2) / 3;       // groups of three columns
+    static constexpr int Q = NW >= 4 ? 4 : NW;  // words per piece
+    static constexpr int H = NW / Q;            // pieces per entry
+    static constexpr int WORDS = G * 8 * NW;
+};
+
+template <int NW>
+__device__ __forceinline__ void russians_build(const u32 *__restrict__ M, u32 *T)
+{
+    typedef Russians<NW> RT;
+    for (int i = threadIdx.x; i < RT::WORDS; i += blockDim.x) {
+        const int q = i % RT::Q, e = (i / RT::Q) % 8, gh = i / (RT::Q * 8);
+        const int h = gh % RT::H, g = gh / RT::H;
+        const int word = h * RT::Q + q;
+        u32 x = 0u;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int col = 3 * g + b;
+            if (((e >> b) & 1) && col < RT::n) x ^= __ldg(M + (size_t)col * NW + word);
+        }
+        T[i] = x;
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void russians_matvec(const u32 *T, const u32 (&v)[NW], u32 (&r)[NW])
+{
+    typedef Russians<NW> RT;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) r[w] = 0u;
+#pragma unroll
+    for (int g = 0; g < RT::G; ++g) {
+        const int bit = 3 * g, w = bit >> 5, sh = bit & 31;
+        u32 e;
+        if (sh <= 29 || w + 1 >= NW) e = (v[w] >> sh) & 7u;
+        else e = __funnelshift_r(v[w], v[w + 1], sh) & 7u;
+#pragma unroll
+        for (int h = 0; h < RT::H; ++h) {
+            const u32 *piece = T + ((g * RT::H + h) * 8) * RT::Q + e * RT::Q;
+            if constexpr (RT::Q == 4) {
+                const uint4 t = *reinterpret_cast<const uint4 *>(piece);
+                r[4 * h] ^= t.x; r[4 * h + 1] ^= t.y; r[4 * h + 2] ^= t.z; r[4 * h + 3] ^= t.w;
+            } else {
+                const uint2 t = *reinterpret_cast<const uint2 *>(piece);
+                r[0] ^= t.x; r[1] ^= t.y;
+            }
+        }
+    }
+}
+
 // One level: for every parent p (index p * 512 * stride) and j in 1 .. 511,
 // states[p * 512 * stride + j * stride] = P[j] states[p * 512 * stride].  The
-// CTA shares j (blockIdx.y + 1) and stages P[j] in shared memory.
+// CTA shares j (blockIdx.y + 1), builds the Four-Russians tables of P[j] in
+// shared memory and handles two parents per thread.
+constexpr int STREAMS_PER_THREAD = 2;
+
 template <int NW>
 __global__ void __launch_bounds__(256)
     k_streams_level(const u32 *__restrict__ P, u32 *states, size_t S, size_t stride, size_t nparents)
 {
-    constexpr int n = NW * 32;
-    __shared__ __align__(16) u32 M[n * NW];
+    typedef Russians<NW> RT;
+    __shared__ __align__(16) u32 T[RT::WORDS];
     const int j = blockIdx.y + 1;
-    const u32 *src = P + (size_t)j * n * NW;
-    for (int t = threadIdx.x; t < n * NW / 4; t += blockDim.x)
-        reinterpret_cast<uint4 *>(M)[t] = reinterpret_cast<const uint4 *>(src)[t];
+    russians_build<NW>(P + (size_t)j * RT::n * NW, T);
     __syncthreads();
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nparents) return;
-    const size_t parent = p * PSET_SIZE * stride;
-    const size_t child = parent + (size_t)j * stride;
-    if (child >= S) return;
-    u32 v[NW], r[NW];
-    load_vec<NW>(v, states + parent * NW);
-    f2_matvec<NW, true>(M, v, r);
-    store_vec<NW>(r, states + child * NW);
+#pragma unroll
+    for (int k = 0; k < STREAMS_PER_THREAD; ++k) {
+        const size_t p = ((size_t)blockIdx.x * STREAMS_PER_THREAD + k) * blockDim.x + threadIdx.x;
+        if (p >= nparents) return;
+        const size_t parent = p * PSET_SIZE * stride;
+        const size_t child = parent + (size_t)j * stride;
+        if (child >= S) continue;
+        u32 v[NW], r[NW];
+        load_vec<NW>(v, states + parent * NW);
+        russians_matvec<NW>(T, v, r);
+        store_vec<NW>(r, states + child * NW);
+    }
 }
 
 cudaError_t launch_streams_psets(int engine, const uint32_t *sets3, void *states, size_t S,
@@ -380,7 +444,8 @@ cudaError_t launch_streams_psets(int engine, const uint32_t *sets3, void *states
         const size_t stride = (size_t)1 << (PSET_BITS * l);
         const size_t span = stride * PSET_SIZE;
         const size_t nparents = (S + span - 1) / span;
-        const dim3 grid((unsigned)((nparents + 255) / 256), PSET_SIZE - 1);
+        const size_t per_cta = (size_t)256 * STREAMS_PER_THREAD;
+        const dim3 grid((unsigned)((nparents + per_cta - 1) / per_cta), PSET_SIZE - 1);
         const uint32_t *P = sets3 + (size_t)l * set_words;
         if (n == 256) k_streams_level<8><<<grid, 256, 0, stream>>>(P, (u32 *)states, S, stride, nparents);
         else if (n == 128) k_streams_level<4><<<grid, 256, 0, stream>>>(P, (u32 *)states, S, stride, nparents);
