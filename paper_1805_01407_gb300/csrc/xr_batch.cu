@@ -97,32 +97,36 @@ __global__ void k_batch_seed(BatchDev d, size_t nreq)
 
 // One level of the power-set scheme over many requests of one engine:
 // segstates[parent + j * stride] = P[j] segstates[parent] when inside the
-// request (below `limit`).  The CTA shares j and stages P[j] in shared memory.
+// request (below `limit`).  The CTA shares j, builds the Four-Russians tables
+// of P[j] in shared memory and handles two items per thread.
+constexpr int BLEVEL_ITEMS_PER_THREAD = 2;
+
 template <int NW>
 __global__ void __launch_bounds__(256)
     k_batch_level(const u32 *__restrict__ P, const BLevelItem *__restrict__ items, size_t nitems,
                   u64 stride, u32 *segstates)
 {
-    constexpr int n = NW * 32;
-    __shared__ __align__(16) u32 M[n * NW];
+    typedef Russians<NW> RT;
+    __shared__ __align__(16) u32 T[RT::WORDS];
     const int j = blockIdx.y + 1;
-    const u32 *src = P + (size_t)j * n * NW;
-    for (int t = threadIdx.x; t < n * NW / 4; t += blockDim.x)
-        reinterpret_cast<uint4 *>(M)[t] = reinterpret_cast<const uint4 *>(src)[t];
+    russians_build<NW>(P + (size_t)j * RT::n * NW, T);
     __syncthreads();
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nitems) return;
-    const BLevelItem it = items[idx];
-    const u64 child = it.parent + (u64)j * stride;
-    if (child >= it.limit) return;
-    u32 v[NW], r[NW];
-    const u32 *ps = segstates + it.parent * SLOT_WORDS;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) v[w] = ps[w];
-    f2_matvec<NW, true>(M, v, r);
-    u32 *cs = segstates + child * SLOT_WORDS;
+    for (int k = 0; k < BLEVEL_ITEMS_PER_THREAD; ++k) {
+        const size_t idx = ((size_t)blockIdx.x * BLEVEL_ITEMS_PER_THREAD + k) * blockDim.x + threadIdx.x;
+        if (idx >= nitems) return;
+        const BLevelItem it = items[idx];
+        const u64 child = it.parent + (u64)j * stride;
+        if (child >= it.limit) continue;
+        u32 v[NW], r[NW];
+        const u32 *ps = segstates + it.parent * SLOT_WORDS;
 #pragma unroll
-    for (int w = 0; w < SLOT_WORDS; ++w) cs[w] = w < NW ? r[w % NW] : 0u;
+        for (int w = 0; w < NW; ++w) v[w] = ps[w];
+        russians_matvec<NW>(T, v, r);
+        u32 *cs = segstates + child * SLOT_WORDS;
+#pragma unroll
+        for (int w = 0; w < SLOT_WORDS; ++w) cs[w] = w < NW ? r[w % NW] : 0u;
+    }
 }
 
 // ---------------------------------------------------------------- persistent fill
@@ -558,7 +562,8 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
         const int n = engine_bits(L.engine);
         const size_t set_words = (size_t)PSET_SIZE * n * (n / 32);
         const uint32_t *P = pset_sets(ctx, L.engine, di) + (size_t)L.level * set_words;
-        const dim3 grid((unsigned)((L.count + 255) / 256), PSET_SIZE - 1);
+        const size_t per_cta = (size_t)256 * BLEVEL_ITEMS_PER_THREAD;
+        const dim3 grid((unsigned)((L.count + per_cta - 1) / per_cta), PSET_SIZE - 1);
         const u64 stride = 1ull << (PSET_BITS * L.level);
         if (n == 256)
             k_batch_level<8><<<grid, 256, 0, st>>>(P, items + L.first, L.count, stride, dp.segstates);

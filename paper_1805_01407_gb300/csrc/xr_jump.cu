@@ -343,66 +343,6 @@ cudaError_t launch_build_power_sets(int engine, const uint32_t *tables, const in
     return err;
 }
 
-// Four-Russians tables of one F2 matrix (n columns of NW words): for each
-// group of three consecutive columns 3g .. 3g+2, the XOR of every subset (8
-// entries), so a matrix-vector product is n/3 table reads instead of n
-// masked XORs.  An entry is split into 16-byte pieces (8-byte for NW = 2);
-// piece h of the 8 entries of a group is stored contiguously (128 or 64
-// bytes), so any lanes of a quarter-warp (half-warp) reading entries of one
-// group hit distinct banks.
-template <int NW>
-struct Russians {
-    static constexpr int n = NW * 32;
-    static constexpr int G = (n + 2) / 3;       // groups of three columns
-    static constexpr int Q = NW >= 4 ? 4 : NW;  // words per piece
-    static constexpr int H = NW / Q;            // pieces per entry
-    static constexpr int WORDS = G * 8 * NW;
-};
-
-template <int NW>
-__device__ __forceinline__ void russians_build(const u32 *__restrict__ M, u32 *T)
-{
-    typedef Russians<NW> RT;
-    for (int i = threadIdx.x; i < RT::WORDS; i += blockDim.x) {
-        const int q = i % RT::Q, e = (i / RT::Q) % 8, gh = i / (RT::Q * 8);
-        const int h = gh % RT::H, g = gh / RT::H;
-        const int word = h * RT::Q + q;
-        u32 x = 0u;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const int col = 3 * g + b;
-            if (((e >> b) & 1) && col < RT::n) x ^= __ldg(M + (size_t)col * NW + word);
-        }
-        T[i] = x;
-    }
-}
-
-template <int NW>
-__device__ __forceinline__ void russians_matvec(const u32 *T, const u32 (&v)[NW], u32 (&r)[NW])
-{
-    typedef Russians<NW> RT;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) r[w] = 0u;
-#pragma unroll
-    for (int g = 0; g < RT::G; ++g) {
-        const int bit = 3 * g, w = bit >> 5, sh = bit & 31;
-        u32 e;
-        if (sh <= 29 || w + 1 >= NW) e = (v[w] >> sh) & 7u;
-        else e = __funnelshift_r(v[w], v[w + 1], sh) & 7u;
-#pragma unroll
-        for (int h = 0; h < RT::H; ++h) {
-            const u32 *piece = T + ((g * RT::H + h) * 8) * RT::Q + e * RT::Q;
-            if constexpr (RT::Q == 4) {
-                const uint4 t = *reinterpret_cast<const uint4 *>(piece);
-                r[4 * h] ^= t.x; r[4 * h + 1] ^= t.y; r[4 * h + 2] ^= t.z; r[4 * h + 3] ^= t.w;
-            } else {
-                const uint2 t = *reinterpret_cast<const uint2 *>(piece);
-                r[0] ^= t.x; r[1] ^= t.y;
-            }
-        }
-    }
-}
-
 // One level: for every parent p (index p * 512 * stride) and j in 1 .. 511,
 // states[p * 512 * stride + j * stride] = P[j] states[p * 512 * stride].  The
 // CTA shares j (blockIdx.y + 1), builds the Four-Russians tables of P[j] in
