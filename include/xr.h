@@ -111,10 +111,16 @@ typedef struct xr_ctx xr_ctx;
 /* ---- context ----------------------------------------------------------- */
 
 /* Create a context on `device` (made current on the calling thread).  Builds
- * the jump tables T^(2^k), k = 0 .. n-1, of every engine on the device by
- * stepping unit states (column j of T is the step of e_j, Sec. 3) and repeated
- * squaring; waits for them.  About 3 MiB of device memory.  Returns
- * XR_ENOMEM / XR_ECUDA on failure, with *out = NULL. */
+ * the jump tables T^(2^k), k = 0 .. n-1, of the 64- to 256-bit engines on the
+ * device by stepping unit states (column j of T is the step of e_j, Sec. 3)
+ * and repeated squaring, and their power sets for stream starts; waits for
+ * them.  About 90 MiB of device memory; the xoshiro512 and xoroshiro1024
+ * tables (16 MiB and 128 MiB) are built on their first use.  Returns
+ * XR_ENOMEM / XR_ECUDA on failure, with *out = NULL.
+ *
+ * Every later call that takes a context, or a batch or server made from one,
+ * runs on the context's device: it makes that device current for the call and
+ * restores the caller's current device before returning. */
 int xr_ctx_create(int device, xr_ctx **out);
 
 /* Free everything the context owns.  Waits for the device first.  NULL is

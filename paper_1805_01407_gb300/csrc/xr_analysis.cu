@@ -416,6 +416,7 @@ extern "C" int xr_linear_complexity_many(xr_ctx *ctx, const xr_lc_job *jobs, siz
                                          uint64_t *h_lc, void *stream)
 {
     if (!ctx || (njobs && (!jobs || !d_states || !d_scratch || !h_lc))) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     if (njobs > (1u << 20) || ((uintptr_t)d_states % 16) || (state_stride % 16) ||
         ((uintptr_t)d_scratch % 16))
         return XR_EINVAL;
@@ -431,6 +432,7 @@ extern "C" int xr_linear_complexity(xr_ctx *ctx, int variant, int bit, size_t N,
                                     void *d_scratch, size_t scratch_bytes, uint64_t *h_lc, void *stream)
 {
     if (!ctx || !d_state || !h_lc || !d_scratch) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     xr_lc_job job;
     job.variant = variant;
     job.bit = bit;
@@ -448,6 +450,7 @@ extern "C" int xr_linear_complexity(xr_ctx *ctx, int variant, int bit, size_t N,
 extern "C" int xr_zeroland(xr_ctx *ctx, int variant, size_t nout, size_t window, uint64_t *d_counts, void *stream)
 {
     if (!ctx || variant < 0 || variant >= XR_NUM_VARIANTS || !d_counts) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     if (window < 1 || window > 64 || nout < window || nout > ((size_t)1 << 32)) return XR_EINVAL;
     if ((uintptr_t)d_counts % 8) return XR_EINVAL;
     const cudaStream_t st = (cudaStream_t)stream;

@@ -222,7 +222,7 @@ const uint32_t *pset_sets(const xr_ctx *ctx, int engine, int di)
 extern "C" int xr_ctx_destroy(xr_ctx *ctx)
 {
     if (!ctx) return XR_OK;
-    cudaSetDevice(ctx->device);
+    DeviceScope dscope(ctx->device);
     cudaDeviceSynchronize();
     for (int e = 0; e < NUM_ENGINES; ++e) {
         cudaFree(ctx->tables[e]);
@@ -291,6 +291,7 @@ extern "C" int xr_ctx_create(int device, xr_ctx **out)
 extern "C" int xr_status(xr_ctx *ctx, int reset)
 {
     if (!ctx) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     int h = 0;
     if (cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return XR_ECUDA;
@@ -301,6 +302,7 @@ extern "C" int xr_status(xr_ctx *ctx, int reset)
 extern "C" int xr_jump_table(xr_ctx *ctx, int variant, int k, void *h_out)
 {
     if (!ctx || !variant_ok(variant) || !h_out) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     {
         const int erc = ensure_engine(ctx, engine_of(variant));
         if (erc != XR_OK) return erc;
@@ -318,6 +320,7 @@ extern "C" int xr_jump_table(xr_ctx *ctx, int variant, int k, void *h_out)
 extern "C" int xr_seed(xr_ctx *ctx, int variant, uint64_t seed, void *d_state, void *stream)
 {
     if (!ctx || !variant_ok(variant) || !d_state || ((uintptr_t)d_state % 16)) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     return status_of(launch_seed(variant, NULL, seed, 1, d_state, ctx->d_status, (cudaStream_t)stream));
 }
 
@@ -325,6 +328,7 @@ extern "C" int xr_seed_many(xr_ctx *ctx, int variant, const uint64_t *d_seeds, s
                             void *d_states, void *stream)
 {
     if (!ctx || !variant_ok(variant)) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     if (count == 0) return XR_OK;
     if (!d_seeds || !d_states || ((uintptr_t)d_states % 16) || ((uintptr_t)d_seeds % 8))
         return XR_EINVAL;
@@ -334,6 +338,7 @@ extern "C" int xr_seed_many(xr_ctx *ctx, int variant, const uint64_t *d_seeds, s
 extern "C" int xr_set_state(xr_ctx *ctx, int variant, const void *h_words, void *d_state, void *stream)
 {
     if (!ctx || !variant_ok(variant) || !h_words || !d_state) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     const int nb = xr_state_bytes(variant);
     unsigned char any = 0;
     for (int b = 0; b < nb; ++b) any |= ((const unsigned char *)h_words)[b];
@@ -345,6 +350,7 @@ extern "C" int xr_set_state(xr_ctx *ctx, int variant, const void *h_words, void 
 extern "C" int xr_get_state(xr_ctx *ctx, int variant, const void *d_state, void *h_words, void *stream)
 {
     if (!ctx || !variant_ok(variant) || !h_words || !d_state) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     cudaError_t e = cudaMemcpyAsync(h_words, d_state, (size_t)xr_state_bytes(variant),
                                     cudaMemcpyDeviceToHost, (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
@@ -369,6 +375,7 @@ extern "C" int xr_jump(xr_ctx *ctx, int variant, int kind, void *d_states, size_
                        uint64_t times, void *stream)
 {
     if (!ctx || !variant_ok(variant) || (kind != XR_JUMP && kind != XR_LONG_JUMP)) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     if (count == 0 || times == 0) return XR_OK;
     if (!states_ok(d_states)) return XR_EINVAL;
     {
@@ -384,6 +391,7 @@ extern "C" int xr_advance(xr_ctx *ctx, int variant, void *d_states, size_t count
                           void *stream)
 {
     if (!ctx || !variant_ok(variant)) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     if (count == 0 || nsteps == 0) return XR_OK;
     if (!states_ok(d_states)) return XR_EINVAL;
     {
@@ -418,6 +426,7 @@ extern "C" int xr_make_streams(xr_ctx *ctx, int variant, int kind, const void *d
                                size_t S, void *d_states_out, void *stream)
 {
     if (!ctx || !variant_ok(variant) || (kind != XR_JUMP && kind != XR_LONG_JUMP)) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     if (S == 0) return XR_OK;
     if (!states_ok(d_base) || !states_ok(d_states_out)) return XR_EINVAL;
     const size_t sb = (size_t)xr_state_bytes(variant);
@@ -450,6 +459,7 @@ extern "C" int xr_fill(xr_ctx *ctx, int variant, void *d_states, size_t S, size_
                        int layout, void *d_out, int write_back, void *stream)
 {
     if (!ctx || !fill_args_ok(variant, d_states, S, m, dtype, layout, d_out)) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     if (S == 0 || m == 0) return XR_OK;
     return status_of(launch_fill(variant, dtype, layout, d_states, S, m, m, d_out, write_back,
                                  ctx->d_status, (cudaStream_t)stream, ctx->encode));
@@ -472,6 +482,7 @@ extern "C" int xr_fill_seq(xr_ctx *ctx, int variant, void *d_state, size_t n, in
                            void *stream)
 {
     if (!ctx || !variant_ok(variant) || !dtype_ok(variant, dtype)) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     if (n == 0) return XR_OK;
     const size_t es = (size_t)xr_dtype_bytes(dtype);
     if (!states_ok(d_state) || !d_out || ((uintptr_t)d_out % es)) return XR_EINVAL;
@@ -506,6 +517,7 @@ extern "C" int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_ba
                             size_t S, size_t m, int dtype, void *h_out, void *stream)
 {
     if (!ctx || !variant_ok(variant) || !dtype_ok(variant, dtype) || !h_base) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     if (kind != XR_JUMP && kind != XR_LONG_JUMP) return XR_EINVAL;
     if (S == 0 || m == 0) return XR_OK;
     if (!h_out) return XR_EINVAL;
@@ -598,6 +610,7 @@ extern "C" int xr_fill_seq_noalloc(xr_ctx *ctx, int variant, void *d_state, size
                                    void *d_out, void *stream)
 {
     if (!ctx || !variant_ok(variant) || !dtype_ok(variant, dtype)) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
     if (n > (size_t)XR_NOALLOC_MAX_OUTPUTS) return XR_EINVAL;
     if (n == 0) return XR_OK;
     const size_t es = (size_t)xr_dtype_bytes(dtype);

@@ -575,12 +575,9 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
         err = cudaGetLastError();
     }
     if (err != cudaSuccess || p.tasks.empty()) return err;
-    static bool attr = false;
-    if (!attr) {
-        err = cudaFuncSetAttribute(k_batch_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (err != cudaSuccess) return err;
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    err = set_smem_once(attr, k_batch_fill, 227 * 1024);
+    if (err != cudaSuccess) return err;
     int per_sm = 0, sms = 0;
     const size_t smem = batch_smem_bytes(opt, block);
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_fill, block, smem);
@@ -624,7 +621,7 @@ static int st_of(cudaError_t e)
 extern "C" int xr_batch_destroy(xr_batch *b)
 {
     if (!b) return XR_OK;
-    cudaSetDevice(b->ctx->device);
+    DeviceScope dscope(b->ctx->device);
     cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
@@ -644,8 +641,8 @@ extern "C" int xr_batch_create(xr_ctx *ctx, const xr_request *h_reqs, size_t nre
     xr_batch *b = new xr_batch();
     b->ctx = ctx;
     build_plan(h_reqs, nreq, b->plan);
-    cudaError_t err = cudaSetDevice(ctx->device);
-    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    DeviceScope dscope(ctx->device);
+    cudaError_t err = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (err == cudaSuccess) err = upload_plan(b->plan, b->dev, b->cap);
     if (err == cudaSuccess) err = cudaStreamSynchronize(b->cap);
     if (err != cudaSuccess) {
@@ -688,6 +685,7 @@ extern "C" int xr_batch_run(xr_batch *b, const uint64_t *d_seeds, void *d_slots,
 {
     if (!b) return XR_EINVAL;
     if (b->plan.reqs.empty()) return XR_OK;
+    DeviceScope dscope(b->ctx->device);
     if (!d_slots || ((uintptr_t)d_slots % 16)) return XR_EINVAL;
     if (b->plan.arena_bytes && (!d_out || ((uintptr_t)d_out % 16))) return XR_EINVAL;
     const cudaStream_t st = (cudaStream_t)stream;
@@ -719,6 +717,7 @@ extern "C" int xr_batch_tune(xr_batch *b, const uint64_t *d_seeds, void *d_slots
                              float *best_ms)
 {
     if (!b || !d_slots) return XR_EINVAL;
+    DeviceScope dscope(b->ctx->device);
     const cudaStream_t st = (cudaStream_t)stream;
     const size_t nbytes = (size_t)(b->plan.max_slot + 1) * 32;
     cudaError_t err = cudaSuccess;

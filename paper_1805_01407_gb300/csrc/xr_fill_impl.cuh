@@ -192,16 +192,10 @@ cudaError_t launch_fill_vd(int layout, void *states, size_t S, size_t m, size_t 
         count_launch();
         return cudaGetLastError();
     }
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e1 = cudaFuncSetAttribute(k_fill_tma<V, DT>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, FILL_SMEM);
-        cudaError_t e2 = cudaFuncSetAttribute(k_fill_plain<V, DT>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, FILL_SMEM);
-        if (e1 != cudaSuccess) return e1;
-        if (e2 != cudaSuccess) return e2;
-        attr_done = true;
-    }
+    static std::atomic<uint64_t> attr_tma{0}, attr_plain{0};
+    cudaError_t ea = set_smem_once(attr_tma, k_fill_tma<V, DT>, FILL_SMEM);
+    if (ea == cudaSuccess) ea = set_smem_once(attr_plain, k_fill_plain<V, DT>, FILL_SMEM);
+    if (ea != cudaSuccess) return ea;
     const size_t rows_per_cta = (size_t)FILL_WARPS * 32;
     const size_t grid = (S + rows_per_cta - 1) / rows_per_cta;
     // The tile store clips columns past the extent only to a 16-byte boundary

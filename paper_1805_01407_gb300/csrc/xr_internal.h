@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "xr.h"
 
 namespace xr {
@@ -101,4 +103,39 @@ int ensure_engine(xr_ctx *ctx, int engine);
 int pset_index(int engine, int d);
 // The three level sets of distance index di of an engine.
 const uint32_t *pset_sets(const xr_ctx *ctx, int engine, int di);
+// Makes the context's device current for the duration of an entry point and
+// restores the caller's device afterwards (nothing to do when they agree), so
+// calls on contexts of different devices need no cudaSetDevice from the caller.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int device)
+    {
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && cur != device && cudaSetDevice(device) == cudaSuccess)
+            prev = cur;
+    }
+    ~DeviceScope()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope &) = delete;
+    DeviceScope &operator=(const DeviceScope &) = delete;
+};
+
+// Raises a kernel's dynamic shared-memory limit on the current device once.
+// The attribute belongs to the kernel in each device's context, so `done`
+// keeps one bit per device; concurrent first calls both set it, harmlessly.
+template <typename Kernel>
+cudaError_t set_smem_once(std::atomic<uint64_t> &done, Kernel kernel, int bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
 }  // namespace xr

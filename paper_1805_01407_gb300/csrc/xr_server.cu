@@ -510,7 +510,7 @@ extern "C" int xr_server_destroy(xr_server *s)
         s->stop.store(true, std::memory_order_release);
         s->th.join();
     }
-    cudaSetDevice(s->ctx->device);
+    DeviceScope dscope(s->ctx->device);
     cudaDeviceSynchronize();
     for (Round &R : s->rounds) {
         free_devplan(R.dev);
@@ -550,7 +550,8 @@ extern "C" int xr_server_create(xr_ctx *ctx, const xr_server_config *cfg, const 
     s->cfg = *cfg;
     s->cvar.assign(h_client_variants, h_client_variants + cfg->nclients);
     s->alloc.init(cfg->arena_bytes);
-    cudaError_t err = cudaSetDevice(ctx->device);
+    DeviceScope dscope(ctx->device);
+    cudaError_t err = cudaSuccess;
     int *d_var = nullptr;
     u64 *d_seed = nullptr;
     if (err == cudaSuccess) err = cudaMalloc((void **)&s->d_cstates, (size_t)cfg->nclients * 32);
@@ -672,6 +673,7 @@ extern "C" void *xr_server_arena(xr_server *s) { return s ? s->arena : nullptr; 
 extern "C" int xr_server_read(xr_server *s, uint64_t offset, uint64_t bytes, void *dst, void *stream)
 {
     if (!s || (bytes && !dst) || offset + bytes > s->cfg.arena_bytes) return XR_EINVAL;
+    DeviceScope dscope(s->ctx->device);
     cudaError_t err = cudaMemcpyAsync(dst, s->arena + offset, bytes, cudaMemcpyDefault, (cudaStream_t)stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize((cudaStream_t)stream);
     return sst(err);
@@ -680,6 +682,7 @@ extern "C" int xr_server_read(xr_server *s, uint64_t offset, uint64_t bytes, voi
 extern "C" int xr_server_client_state(xr_server *s, uint32_t client, void *h_words)
 {
     if (!s || !h_words || client >= s->cfg.nclients) return XR_EINVAL;
+    DeviceScope dscope(s->ctx->device);
     cudaError_t err = cudaStreamSynchronize(s->admit_st);
     unsigned char buf[32];
     if (err == cudaSuccess) err = cudaMemcpy(buf, s->d_cstates + (size_t)client * 8, 32, cudaMemcpyDeviceToHost);
