@@ -2,8 +2,9 @@
 ("Scrambled Linear Pseudorandom Number Generators", arXiv 1805.01407).
 
 TEST INFRASTRUCTURE ONLY.  The library (``paper_1805_01407_gb300``) never imports
-this package.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
-leg of ``bench.py`` may import it.  It shares no code with the CUDA path.
+this package.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of
+``bench.py`` (the baseline beside the device numbers and the reference arm) may
+import it.  It shares no code with the CUDA path.
 
 The arithmetic lives in ``xr_oracle.c`` (plain C, compiled here with gcc); this
 module only marshals arguments and orchestrates the definitions:
@@ -15,7 +16,9 @@ module only marshals arguments and orchestrates the definitions:
 * ``char_poly`` -- Berlekamp-Massey on bit 0 of the ``+`` output (Sec. 4.1, 6);
 * ``jump``/``jump_pow``/``streams`` -- T^J s = sum c_i T^i s with
   x^J mod p(x) = sum c_i x^i (Sec. 6, Cayley-Hamilton);
-* matrix helpers -- T from the step or from the paper's block matrices (Sec. 3).
+* matrix helpers -- T from the step or from the paper's block matrices (Sec. 3);
+* ``linear_complexity`` -- Berlekamp-Massey on one output bit (Sec. 9.3, Table 13);
+* ``zeroland`` -- one bits in windows of outputs from every one-bit state (Sec. 8).
 
 Jump distances are not printed in the paper.  Reading used here: a jump
 advances 2^(n/2) steps and a long jump 2^(3n/4) steps for an n-bit state

@@ -3,8 +3,9 @@
  * "Scrambled Linear Pseudorandom Number Generators" (ACM TOMS, arXiv 1805.01407).
  *
  * TEST INFRASTRUCTURE ONLY.  The library never links, loads or calls this file.
- * Only the tests, the smoke check of the build entry and the CPU-baseline leg of
- * the benchmark may load it.  It shares no code, header, table or constant with
+ * Only the tests, the smoke check of the build entry and the benchmark's CPU
+ * legs (the baseline beside the device numbers and the reference arm) may
+ * load it.  It shares no code, header, table or constant with
  * the CUDA path: every parameter below is typed here from the paper's tables.
  *
  * Everything is the plain definition, computed one value at a time:
@@ -24,7 +25,9 @@
  *   - F2 matrices T (transition as a map on column vectors of state bits), the
  *     characteristic polynomial (Sec. 6), Berlekamp-Massey (Sec. 6, Sec. 9.3),
  *     polynomial arithmetic over F2 and jumps as T^J s = sum_i c_i T^i s with
- *     x^J mod p(x) = sum_i c_i x^i (Sec. 6, Cayley-Hamilton).
+ *     x^J mod p(x) = sum_i c_i x^i (Sec. 6, Cayley-Hamilton);
+ *   - the escaping-zeroland counts of Sec. 8 (one bits in windows of outputs
+ *     from every state with one bit set).
  *
  * Bit convention.  A state of k words of w bits is the column vector whose bit
  * index is word * w + b, where b is the machine bit (b = 0 is the least

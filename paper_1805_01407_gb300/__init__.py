@@ -377,7 +377,10 @@ class Context:
         of ints, None where N bits cannot decide the complexity."""
         import torch
         arr = (LcJob * max(len(jobs), 1))(*[LcJob(_v(v), b, n) for (v, b, n) in jobs])
-        _need(d_states, (len(jobs) - 1) * state_stride + 16 if jobs else 0, "d_states")
+        if state_stride % 16 or any(state_stride < state_bytes(v) for (v, _, _) in jobs[:-1]):
+            raise ValueError("state_stride must be a multiple of 16 and hold every state")
+        _need(d_states, max((j * state_stride + state_bytes(v) for j, (v, _, _) in enumerate(jobs)), default=0),
+              "d_states")
         nbytes = lib().xr_lc_scratch_bytes(arr, len(jobs))
         scratch = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=self.device)
         out = (ctypes.c_uint64 * max(len(jobs), 1))()
