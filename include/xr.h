@@ -294,7 +294,10 @@ int xr_batch_tune(xr_batch *b, const uint64_t *d_seeds, void *d_slots, void *d_o
  * continue one sequence in submission order whatever runs concurrently.
  * Admitted requests run as rounds of the batched kernels of xr_batch_*;
  * up to max_rounds rounds are in flight on separate streams, so requests that
- * arrive while others run are admitted and overlap on the device.  Outputs
+ * arrive while others run are admitted and overlap on the device.  A round
+ * takes at most arena_bytes / max_rounds bytes of outputs (a single larger
+ * request forms a round alone), so under load the next round is admitted
+ * while the current one runs.  Outputs
  * stay in the arena until released.  Plain mode instead runs one
  * xr_fill_seq per request, in arrival order, on one stream (for comparison). */
 #define XR_SERVE_BATCHED 0

@@ -438,10 +438,17 @@ static void scheduler(xr_server *s)
                 R.tickets.clear();
                 R.clients.clear();
                 R.reqs.clear();
+                // A round takes at most its share of the arena, so the rounds in
+                // flight divide the memory and the next one is admitted while
+                // the current one runs (a larger request still goes alone).
+                const u64 share = s->cfg.arena_bytes / s->cfg.max_rounds;
+                u64 round_bytes = 0;
                 while (!s->pending.empty() && R.tickets.size() < s->cfg.max_round_requests) {
                     SReq &q = s->reqs[s->pending.front()];
+                    if (!R.tickets.empty() && round_bytes + q.bytes > share) break;
                     u64 off;
                     if (!s->alloc.alloc(q.bytes, &off)) break;  // arrival order: wait for memory
+                    round_bytes += q.bytes;
                     q.off = off;
                     q.state = S_ADMITTED;
                     const u32 i = (u32)R.tickets.size();
