@@ -588,6 +588,14 @@ extern "C" int xr_server_create(xr_ctx *ctx, const xr_server_config *cfg, const 
             if (err == cudaSuccess) err = cudaEventCreateWithFlags(&R.admitted, cudaEventDisableTiming);
             if (err == cudaSuccess) err = cudaEventCreateWithFlags(&R.done, cudaEventDisableTiming);
             if (err == cudaSuccess) err = cudaMalloc((void **)&R.d_slots, (size_t)cfg->max_round_requests * 32);
+            // admission records for the largest round (a round has at most as
+            // many clients as requests), so no round reallocates them
+            if (err == cudaSuccess) {
+                const size_t ca = (size_t)cfg->max_round_requests * sizeof(AdmitClient);
+                R.admit_cap = ((ca + 255) & ~(size_t)255) + (size_t)cfg->max_round_requests * sizeof(AdmitReq) + 256;
+                err = cudaMalloc((void **)&R.d_admit, R.admit_cap);
+                if (err == cudaSuccess) err = cudaMallocHost((void **)&R.h_admit, R.admit_cap);
+            }
             // size the plan buffers for the largest round up front
             if (err == cudaSuccess) {
                 R.dev.seg_cap = segcap * 32;
