@@ -220,7 +220,7 @@ __device__ __forceinline__ void batch_warp_rows(const u32 *st, unsigned char *sl
             if (lane == 0) bulk_wait_read<1>();
             __syncwarp();
         }
-        fill_tile_row<G, DT>(e, tile, lane, (size_t)COLS);
+        fill_tile_row<G, DT>(e, tile, lane, (size_t)COLS, true, st, (size_t)j0);  // st is read only here
         fence_proxy_async_shared();
         __syncwarp();
         if (lane == 0) {

@@ -24,11 +24,51 @@ constexpr int FILL_NBUF = 2;           // shared-memory tiles per warp
 constexpr int TILE_BYTES = 32 * 128;   // 32 rows x 128 bytes
 constexpr int FILL_SMEM = FILL_WARPS * FILL_NBUF * TILE_BYTES + 1024;  // + alignment slack
 
+// The double (x >> 11) * 2^-53 of a 64-bit output whose high word is nonzero,
+// with no branch: unit_f64_bits without its rare case.  `hmin` collects the
+// high words; a row whose smallest high word is zero (x < 2^32, probability
+// 2^-32 per value) is regenerated with the exact conversion (redo_row_f64).
+__device__ __forceinline__ u64 unit_f64_bits_hi(u64 x, u32 &hmin)
+{
+    u32 lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(x));
+    hmin = min(hmin, hi);
+    const u32 vl = __funnelshift_r(lo, hi, 11);
+    const u32 vh = hi >> 11;
+    const u32 lz = (u32)__clz(hi);  // 32 when hi == 0; that row is replaced
+    const u32 mh = __funnelshift_l(vl, vh, lz) + ((1021u - lz) << 20);
+    u32 ml;
+    asm("shl.b32 %0, %1, %2;" : "=r"(ml) : "r"(vl), "r"(lz));  // 0 for a shift of 32
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(ml), "r"(mh));
+    return r;
+}
+
+// Regenerate this lane's f64 row at column j0 with the exact conversion: the
+// stream's start state (still in global memory until write-back) stepped j0
+// times.  Taken about once per 2^32 values.
+template <typename G>
+static __device__ __noinline__ void redo_row_f64(u32 row, u32 sw, const void *state0, size_t j0)
+{
+    typename G::E e;
+    load_state(e, state0);
+    for (size_t j = 0; j < j0; ++j) e.step();
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+        u32 w[4];
+        gen16<G, DT_F64>(e, w);
+        st_shared_v4(row + (((u32)c ^ sw) << 4), w[0], w[1], w[2], w[3]);
+    }
+}
+
 // Generate one 32 x 128 B tile row for this lane into the swizzled tile:
 // 16-byte chunk c of row r lives at r * 128 + ((c ^ (r & 7)) * 16), so the 8
-// lanes of each quarter-warp hit 8 different bank groups.
+// lanes of each quarter-warp hit 8 different bank groups.  Full f64 rows of
+// 64-bit generators take the branch-free conversion and the row check above;
+// `state0` and `j0` locate the row for the rare redo (live lanes only).
 template <typename G, int DT>
-__device__ __forceinline__ void fill_tile_row(typename G::E &e, u32 tile, int lane, size_t left)
+__device__ __forceinline__ void fill_tile_row(typename G::E &e, u32 tile, int lane, size_t left, bool live,
+                                              const void *state0, size_t j0)
 {
     typedef typename OutElem<DT>::type OT;
     constexpr int COLS = 128 / (int)sizeof(OT);
@@ -36,11 +76,28 @@ __device__ __forceinline__ void fill_tile_row(typename G::E &e, u32 tile, int la
     const u32 row = tile + (u32)lane * 128u;
     const u32 sw = (u32)(lane & 7);
     if (left >= (size_t)COLS) {
+        if constexpr (DT == DT_F64 && sizeof(typename G::word) == 8) {
+            u32 hmin = 0xffffffffu;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            u32 w[4];
-            gen16<G, DT>(e, w);
-            st_shared_v4(row + (((u32)c ^ sw) << 4), w[0], w[1], w[2], w[3]);
+            for (int c = 0; c < 8; ++c) {
+                u32 w[4];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const u64 o = unit_f64_bits_hi((u64)G::out(e), hmin);
+                    e.step();
+                    w[2 * q] = (u32)o;
+                    w[2 * q + 1] = (u32)(o >> 32);
+                }
+                st_shared_v4(row + (((u32)c ^ sw) << 4), w[0], w[1], w[2], w[3]);
+            }
+            if (__builtin_expect(hmin == 0u, 0) && live) redo_row_f64<G>(row, sw, state0, j0);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                u32 w[4];
+                gen16<G, DT>(e, w);
+                st_shared_v4(row + (((u32)c ^ sw) << 4), w[0], w[1], w[2], w[3]);
+            }
         }
     } else {
         const int cnt = (int)left;
@@ -83,7 +140,7 @@ __global__ void __launch_bounds__(FILL_WARPS * 32)
             if (lane == 0) bulk_wait_read<FILL_NBUF - 1>();
             __syncwarp();
         }
-        fill_tile_row<G, DT>(e, tile, lane, m - j0);
+        fill_tile_row<G, DT>(e, tile, lane, m - j0, live, (const char *)states + i * sizeof(e.s), j0);
         fence_proxy_async_shared();
         __syncwarp();
         if (lane == 0) {
@@ -137,7 +194,7 @@ __global__ void __launch_bounds__(FILL_WARPS * 32)
     }
     const u32 tile = base + (u32)(warp * FILL_NBUF * TILE_BYTES);
     for (size_t j0 = 0; j0 < m; j0 += COLS) {
-        fill_tile_row<G, DT>(e, tile, lane, m - j0);
+        fill_tile_row<G, DT>(e, tile, lane, m - j0, live, (const char *)states + i * sizeof(e.s), j0);
         __syncwarp();
         const int cols = (int)((m - j0) < (size_t)COLS ? (m - j0) : (size_t)COLS);
         for (int f = lane; f < 32 * COLS; f += 32) {

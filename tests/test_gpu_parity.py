@@ -414,3 +414,69 @@ def test_invalid_arguments(ctx, xr):
     assert e.value.status == xr.XR_EINVAL
     with pytest.raises(ValueError):
         ctx.fill("xoshiro256**", t, 1, 17, "u64", out)   # buffer too small
+
+
+# ------------------------------------------------------------------ small outputs inside rows
+
+def _state_before(name, target, k):
+    """T^(-k) target: the state k steps before `target` (the period is 2^n - 1, Sec. 6)."""
+    n = O.state_bits(name)
+    return O.jump_pow(name, 0, (1 << n) - 1 - k, np.array(target, dtype=np.uint64))
+
+
+def _small_output_starts(name, ks, xs):
+    """Start states whose output k (for each k in ks) is the crafted value x."""
+    starts, where = [], []
+    for k in ks:
+        for x in xs:
+            target = [x, 0] if O.state_words(name) == 2 else [x, 0x1234567, 0x89ABCDE, 0]
+            s0 = _state_before(name, target, k)
+            assert int(O.generate(name, s0, k + 1)[0][k]) == x
+            starts.append(s0)
+            where.append((k, x))
+    return np.array(starts, dtype=np.uint64), where
+
+
+@pytest.mark.parametrize("name", ["xoshiro256+", "xoroshiro128+"])
+def test_f64_rows_with_outputs_below_2_32(ctx, xr, name):
+    """Doubles are exact when an output below 2^32 (x >> 11 has no bit in the
+    high word) falls anywhere in a 16-value row, not only at a stream's first
+    output: such rows are regenerated with the exact conversion."""
+    import torch
+    ks = [0, 15, 16, 37, 1000, 1023]
+    starts, _ = _small_output_starts(name, ks, [0, 5, 2**11, 2**31 + 7, 2**32 - 1])
+    S, m = len(starts), 1024
+    raw = O.fill_streams(name, starts, m)
+    for layout in ("stream", "interleaved"):
+        out = ctx.empty_output(S * m, "f64")
+        ctx.fill(name, states_to_device(name, starts), S, m, "f64", out, layout=layout)
+        torch.cuda.synchronize()
+        got = out_to_numpy(out, "f64")
+        want = expected(name, raw, "f64")
+        if layout == "interleaved":
+            want = want.reshape(S, m).T.reshape(-1)
+        assert_bits_equal(got, want, "f64 " + layout)
+
+
+def test_batch_f64_rows_with_outputs_below_2_32(ctx, xr):
+    """The same inside full batch segments (the tile path of xr_batch_run):
+    requests whose slot state puts a small output at output 5000 or 20000."""
+    import torch
+    name = "xoshiro256+"
+    starts, _ = _small_output_starts(name, [5000, 20000, 32767], [3, 2**32 - 1])
+    n = 32 * 1024
+    specs = [(name, "f64", n, r) for r in range(len(starts))]
+    reqs, offs, arena = xr.pack_requests(specs)
+    b = xr.Batch(ctx, reqs)
+    slots = torch.zeros(len(specs) * 32, dtype=torch.uint8)
+    for r, s0 in enumerate(starts):
+        slots[r * 32:(r + 1) * 32] = torch.from_numpy(s0.astype(np.uint64).view(np.uint8).copy())
+    d_slots = slots.cuda()
+    out = torch.zeros(arena, dtype=torch.uint8, device="cuda")
+    b.run(None, d_slots, out)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    for r, s0 in enumerate(starts):
+        raw, _ = O.generate(name, s0, n)
+        assert_bits_equal(o[offs[r]:offs[r] + n * 8].view(np.float64), expected(name, raw, "f64"), "request %d" % r)
+    b.close()
