@@ -59,7 +59,7 @@ extern "C" {
 #define XR_EZERO_STATE 2   /* an all-zero generator state was given or seen */
 #define XR_ENOMEM 3        /* the context could not allocate its own memory */
 #define XR_ECUDA 4         /* a CUDA call failed */
-#define XR_ETIMEOUT 5      /* a bounded device-side wait gave up */
+#define XR_ETIMEOUT 5      /* a bounded wait (xr_server_wait_for) ran out */
 #define XR_EUNSUPPORTED 6  /* valid request this build does not implement */
 
 /* ---- enums ------------------------------------------------------------- */
@@ -333,6 +333,12 @@ int xr_server_submit(xr_server *s, uint32_t client, uint64_t n, int dtype, uint6
  * of the arena (xr_server_arena) until released; *latency_us is the time from
  * submission to observed completion. */
 int xr_server_wait(xr_server *s, uint64_t ticket, uint64_t *out_offset, double *latency_us);
+
+/* As xr_server_wait, but gives up after timeout_us microseconds of host time
+ * (0 polls once) and returns XR_ETIMEOUT, with the request still queued or
+ * running: a caller can bound its wait and detect a stalled server without
+ * any device-side wait.  A later wait on the same ticket is allowed. */
+int xr_server_wait_for(xr_server *s, uint64_t ticket, double timeout_us, uint64_t *out_offset, double *latency_us);
 /* Free a completed request's arena space (its outputs become invalid). */
 int xr_server_release(xr_server *s, uint64_t ticket);
 void *xr_server_arena(xr_server *s);

@@ -127,6 +127,7 @@ def lib():
         L.xr_server_destroy.argtypes = [vp]
         L.xr_server_submit.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint64, i, ctypes.POINTER(ctypes.c_uint64)]
         L.xr_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), dp]
+        L.xr_server_wait_for.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64), dp]
         L.xr_server_release.argtypes = [vp, ctypes.c_uint64]
         L.xr_server_arena.argtypes = [vp]
         L.xr_server_arena.restype = vp
@@ -144,7 +145,7 @@ def lib():
         L.xr_linear_complexity_many.argtypes = [vp, ctypes.POINTER(LcJob), sz, vp, sz, vp, sz,
                                                 ctypes.POINTER(ctypes.c_uint64), vp]
         L.xr_linear_complexity_many.restype = i
-        for fn in ("xr_server_create", "xr_server_destroy", "xr_server_submit", "xr_server_wait",
+        for fn in ("xr_server_create", "xr_server_destroy", "xr_server_submit", "xr_server_wait", "xr_server_wait_for",
                    "xr_server_release", "xr_server_read", "xr_server_client_state", "xr_server_stats",
                    "xr_server_replay"):
             getattr(L, fn).restype = i
@@ -505,9 +506,17 @@ class Server:
         _check(lib().xr_server_submit(self._h, client, n, DTYPES[dtype], ctypes.byref(t)), "xr_server_submit")
         return t.value
 
-    def wait(self, ticket):
+    def wait(self, ticket, timeout_us=None):
+        """(arena offset, latency in us) once the request is complete; with
+        timeout_us, None when it is not complete within that host time."""
         off, lat = ctypes.c_uint64(), ctypes.c_double()
-        _check(lib().xr_server_wait(self._h, ticket, ctypes.byref(off), ctypes.byref(lat)), "xr_server_wait")
+        if timeout_us is None:
+            _check(lib().xr_server_wait(self._h, ticket, ctypes.byref(off), ctypes.byref(lat)), "xr_server_wait")
+            return off.value, lat.value
+        rc = lib().xr_server_wait_for(self._h, ticket, float(timeout_us), ctypes.byref(off), ctypes.byref(lat))
+        if rc == XR_ETIMEOUT:
+            return None
+        _check(rc, "xr_server_wait_for")
         return off.value, lat.value
 
     def release(self, ticket):

@@ -671,6 +671,25 @@ extern "C" int xr_server_wait(xr_server *s, uint64_t ticket, uint64_t *out_offse
     return XR_OK;
 }
 
+extern "C" int xr_server_wait_for(xr_server *s, uint64_t ticket, double timeout_us, uint64_t *out_offset,
+                                  double *latency_us)
+{
+    if (!s || !(timeout_us >= 0.0)) return XR_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return XR_EINVAL;
+    auto ready = [&] { return it->second.state >= S_DONE || s->error != XR_OK; };
+    if (timeout_us >= 1e15) {  // over 30 years: an unbounded wait (and no clock overflow)
+        s->cv.wait(lk, ready);
+    } else if (!s->cv.wait_for(lk, std::chrono::duration<double, std::micro>(timeout_us), ready)) {
+        return XR_ETIMEOUT;
+    }
+    if (it->second.state == S_FAILED || it->second.state < S_DONE) return s->error != XR_OK ? s->error : XR_ECUDA;
+    if (out_offset) *out_offset = it->second.off;
+    if (latency_us) *latency_us = it->second.t_done - it->second.t_sub;
+    return XR_OK;
+}
+
 extern "C" int xr_server_release(xr_server *s, uint64_t ticket)
 {
     if (!s) return XR_EINVAL;

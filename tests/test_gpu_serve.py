@@ -178,3 +178,22 @@ def test_serving_trace_sampled(ctx, xr):
             st = O.jump_pow(names[c], 0, total[c], O.seed(names[c], seeds[c]))
             want = st.astype(np.uint64).tobytes()
             assert srv.client_state(c) == want, c
+
+
+def test_bounded_wait(ctx, xr):
+    """xr_server_wait_for: a request still running returns XR_ETIMEOUT (None
+    here) and stays valid; waiting again completes it with the right outputs."""
+    import torch
+    seeds = [3 + c for c in range(len(CLIENTS))]
+    with xr.Server(ctx, CLIENTS, seeds, arena_bytes=1 << 31, mode="batched") as srv:
+        big = srv.submit(0, 1 << 27, "f64")      # 1 GiB: still running right after submission
+        assert srv.wait(big, timeout_us=0) is None
+        off, lat = srv.wait(big, timeout_us=60e6)
+        got = read(srv, off, 1 << 27, "f64", torch)
+        assert_bits_equal(got[:4096], Expect(seeds).take(0, 4096, "f64"), "head")
+        assert srv.wait(big, timeout_us=0) is not None      # complete: no timeout
+        srv.release(big)
+        with pytest.raises(xr.XRError):
+            srv.wait(big + 1000, timeout_us=1.0)            # no such ticket
+        with pytest.raises(xr.XRError):
+            srv.wait(big, timeout_us=-1.0)                  # bad limit
