@@ -108,7 +108,7 @@ def workload_config(world):
                     "(2^30 values); SplitMix64(42) base; stream i = J^(first+i)(base)",
         "streams": S, "outputs_per_stream": m, "jobs_per_step": len(jobs()),
         "values_per_step": len(jobs()) * S * m, "bytes_per_step": nbytes,
-        "global_batch": world * len(jobs()) * S * m, "seq_len": m,
+        "values_per_step_all_ranks": world * len(jobs()) * S * m,
         "l2": "each launch writes 4-8 GiB, far larger than the 129 MB L2; no flush needed",
         "parallelism": "replicas over disjoint stream ranges" if world > 1 else "single GPU",
     }, nbytes
