@@ -238,6 +238,23 @@ def cpu_baseline(seconds):
             "seconds": t, "bytes": b}
 
 
+def extra_cpu_baseline(streams=64):
+    """The oracle on the other generators of the paper, the same recipe as the
+    extra-generator leg (SplitMix64(42) base, streams J^i, 2^10 outputs each,
+    native word and f64) on `streams` streams per job."""
+    import oracle as O
+    m, seed = W.CONFIG_BULK["m"], W.CONFIG_BULK["seed"]
+    nbytes, t0 = 0, time.perf_counter()
+    for v in W.EXTRA_VARIANTS:
+        raw = O.bulk_fill(v, "jump", O.seed(v, seed), streams, m)
+        O.to_f64(v, raw)
+        nbytes += streams * m * (dtype_bytes(W.native_dtype(v)) + 8)
+    t = time.perf_counter() - t0
+    return {"value": nbytes / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "9 generators x {native, f64} x %d streams x %d outputs, single-threaded plain C, %.2f s"
+                      % (streams, m, t)}
+
+
 def analysis_cpu_baseline():
     """The oracle on the analysis workloads of run_analysis (same inputs)."""
     import oracle as O
@@ -426,6 +443,8 @@ def run_xr(args):
         line["serving"] = run_serving(xr, ctx, args)
     if not args.no_extra:
         line["extra_generators"] = run_extra(xr, ctx, args)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            line["extra_generators"]["cpu_baseline"] = extra_cpu_baseline()
     if not args.no_jumpstart:
         line["jumpstart"] = run_jumpstart(xr, ctx, args)
     if not args.no_analysis:
@@ -496,6 +515,7 @@ def run_batched(xr, ctx, args):
         "workload": "4096 requests, lengths log-uniform in [1, 2^24] (%.1f GB), 8 generators, "
                     "native/f64, SplitMix64(r) seeds; one persistent launch in a CUDA graph" % (nbytes / 1e9),
         "value": nbytes / (batch_ms / 1e3) / 1e9, "unit": UNIT, "ms": batch_ms,
+        "frac_of_measured_peak": nbytes / (batch_ms / 1e3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
         "plain_value": nbytes / (plain_ms[-1] / 1e3) / 1e9, "plain_ms": plain_ms[-1],
         "speedup_vs_plain": plain_ms[-1] / batch_ms,
         "plain_request_ms_p50": q(0.5), "plain_request_ms_p99": q(0.99),
@@ -511,6 +531,7 @@ def run_extra(xr, ctx, args):
     import torch
     S, m, seed = W.CONFIG_BULK["S"], W.CONFIG_BULK["m"], W.CONFIG_BULK["seed"]
     stream = torch.cuda.current_stream()
+    peak = measured_peaks()[0]["hbm_gbs"]
     res = {}
     for v in W.EXTRA_VARIANTS:
         base = ctx.empty_states(v, 1)
@@ -530,7 +551,8 @@ def run_extra(xr, ctx, args):
                 b.synchronize()
                 ts.append(a.elapsed_time(b))
             ms = statistics.median(ts)
-            res["%s/%s" % (v, d)] = {"fill_gbs": S * m * dtype_bytes(d) / (ms / 1e3) / 1e9, "fill_ms": ms}
+            gbs = S * m * dtype_bytes(d) / (ms / 1e3) / 1e9
+            res["%s/%s" % (v, d)] = {"fill_gbs": gbs, "fill_ms": ms, "frac_of_measured_peak": gbs / peak}
             del out
     torch.cuda.synchronize()
     assert ctx.status() == 0
@@ -632,6 +654,7 @@ def run_jumpstart(xr, ctx, args):
         ms_fill = timed(lambda: ctx.fill(v, states, S, m, "u64", out))
         res[kind] = {"streams_ms": ms_streams, "streams_per_s": S / (ms_streams / 1e3),
                      "fill_ms": ms_fill, "fill_gbs": S * m * 8 / (ms_fill / 1e3) / 1e9,
+                     "fill_frac_of_measured_peak": S * m * 8 / (ms_fill / 1e3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
                      "total_gbs": S * m * 8 / ((ms_streams + ms_fill) / 1e3) / 1e9}
     del out, states
     torch.cuda.synchronize()
@@ -667,6 +690,7 @@ def run_serving(xr, ctx, args):
                      "rounds": st["rounds"], "arena_peak_bytes": st["arena_peak"]}
     res["value"] = res["batched"]["value"]
     res["unit"] = UNIT
+    res["saturation_frac_of_measured_peak"] = res["batched"]["saturation_value"] / measured_peaks()[0]["hbm_gbs"]
     res["batched_vs_plain_saturation"] = res["batched"]["saturation_value"] / res["plain"]["saturation_value"]
     return res
 
