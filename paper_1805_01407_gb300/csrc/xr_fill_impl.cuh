@@ -19,10 +19,33 @@
 
 namespace xr {
 
-constexpr int FILL_WARPS = 4;          // warps per CTA
-constexpr int FILL_NBUF = 2;           // shared-memory tiles per warp
+constexpr int FILL_WARPS = 4;          // warps per CTA (plain-store path)
+constexpr int FILL_NBUF = 2;           // shared-memory tiles per warp (plain-store path)
 constexpr int TILE_BYTES = 32 * 128;   // 32 rows x 128 bytes
 constexpr int FILL_SMEM = FILL_WARPS * FILL_NBUF * TILE_BYTES + 1024;  // + alignment slack
+
+// Tile-store path: warps per CTA and tiles in flight per warp, by how much
+// integer work a byte costs.  Measured on GB300 over {1,2,4} warps x {2..8}
+// tiles: outputs that leave the ALU idle (native words, and doubles of 32-bit
+// generators) gain from more tiles per warp in flight behind the TMA unit (6
+// per warp, 2 warps per CTA), while the heavier ones need the warps instead:
+// 4 tiles x 2 warps for the exact doubles of 128-bit states, 3 tiles x 1 warp
+// (the most CTAs per SM) for the doubles of 256-bit and larger states and for
+// every output of xoshiro512 (whose 8-word step is the costliest; the 16-word
+// xoroshiro1024 step touches only 3 words).
+// Short rows (at most FILL_SHORT_TILES tiles, so a warp lives only a few
+// tiles) take 4 warps x 2 tiles instead: there the warps per SM count, not the
+// depth of the store queue.
+constexpr int FILL_SHORT_TILES = 4;
+
+template <int V, int DT, bool SHORT>
+struct FillCfg {
+    static constexpr bool f64w = DT == DT_F64 && sizeof(typename Gen<V>::word) == 8;
+    static constexpr bool heavy = (f64w && Gen<V>::E::NBITS >= 256) || Gen<V>::E::NBITS == 512;
+    static constexpr int WARPS = SHORT ? 4 : heavy ? 1 : 2;
+    static constexpr int NBUF = SHORT ? 2 : heavy ? 3 : (f64w ? 4 : 6);
+    static constexpr int SMEM = WARPS * NBUF * TILE_BYTES + 1024;
+};
 
 // The double (x >> 11) * 2^-53 of a 64-bit output whose high word is nonzero,
 // with no branch: unit_f64_bits without its rare case.  `hmin` collects the
@@ -109,18 +132,19 @@ __device__ __forceinline__ void fill_tile_row(typename G::E &e, u32 tile, int la
     }
 }
 
-template <int V, int DT>
-__global__ void __launch_bounds__(FILL_WARPS * 32)
+template <int V, int DT, bool SHORT>
+__global__ void __launch_bounds__(FillCfg<V, DT, SHORT>::WARPS * 32)
     k_fill_tma(const __grid_constant__ CUtensorMap map, void *states, size_t S, size_t m,
                int write_back, int *status)
 {
     typedef Gen<V> G;
     typedef typename G::E E;
+    typedef FillCfg<V, DT, SHORT> CF;
     constexpr int COLS = 128 / (int)sizeof(typename OutElem<DT>::type);
     extern __shared__ unsigned char dyn_smem[];
     const u32 base = (smem_addr(dyn_smem) + 1023u) & ~1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t row0 = ((size_t)blockIdx.x * FILL_WARPS + warp) * 32;
+    const size_t row0 = ((size_t)blockIdx.x * CF::WARPS + warp) * 32;
     if (row0 >= S) return;
     const size_t i = row0 + lane;
     const bool live = i < S;
@@ -132,12 +156,12 @@ __global__ void __launch_bounds__(FILL_WARPS * 32)
 #pragma unroll
         for (int j = 0; j < E::K; ++j) e.s[j] = 0;
     }
-    const u32 tiles = base + (u32)(warp * FILL_NBUF * TILE_BYTES);
+    const u32 tiles = base + (u32)(warp * CF::NBUF * TILE_BYTES);
     int it = 0;
     for (size_t j0 = 0; j0 < m; j0 += COLS, ++it) {
-        const u32 tile = tiles + (u32)((it % FILL_NBUF) * TILE_BYTES);
-        if (it >= FILL_NBUF) {
-            if (lane == 0) bulk_wait_read<FILL_NBUF - 1>();
+        const u32 tile = tiles + (u32)((it % CF::NBUF) * TILE_BYTES);
+        if (it >= CF::NBUF) {
+            if (lane == 0) bulk_wait_read<CF::NBUF - 1>();
             __syncwarp();
         }
         fill_tile_row<G, DT>(e, tile, lane, m - j0, live, (const char *)states + i * sizeof(e.s), j0);
@@ -148,7 +172,7 @@ __global__ void __launch_bounds__(FILL_WARPS * 32)
             bulk_commit();
         }
     }
-    if (lane == 0) bulk_wait_all<0>();
+    if (lane == 0) bulk_wait_read<0>();  // the tiles may be released; the writes land by the grid's end
     if (write_back && live) store_state(e, (char *)states + i * sizeof(e.s));
 }
 
@@ -249,12 +273,18 @@ cudaError_t launch_fill_vd(int layout, void *states, size_t S, size_t m, size_t 
         count_launch();
         return cudaGetLastError();
     }
-    static std::atomic<uint64_t> attr_tma{0}, attr_plain{0};
-    cudaError_t ea = set_smem_once(attr_tma, k_fill_tma<V, DT>, FILL_SMEM);
+    typedef FillCfg<V, DT, false> CL;
+    typedef FillCfg<V, DT, true> CS;
+    static std::atomic<uint64_t> attr_long{0}, attr_short{0}, attr_plain{0};
+    cudaError_t ea = set_smem_once(attr_long, k_fill_tma<V, DT, false>, CL::SMEM);
+    if (ea == cudaSuccess) ea = set_smem_once(attr_short, k_fill_tma<V, DT, true>, CS::SMEM);
     if (ea == cudaSuccess) ea = set_smem_once(attr_plain, k_fill_plain<V, DT>, FILL_SMEM);
     if (ea != cudaSuccess) return ea;
     const size_t rows_per_cta = (size_t)FILL_WARPS * 32;
     const size_t grid = (S + rows_per_cta - 1) / rows_per_cta;
+    const bool short_rows = (m + COLS - 1) / COLS <= (size_t)FILL_SHORT_TILES;
+    const size_t tma_rows = (size_t)(short_rows ? CS::WARPS : CL::WARPS) * 32;
+    const size_t tma_grid = (S + tma_rows - 1) / tma_rows;
     // The tile store clips columns past the extent only to a 16-byte boundary
     // (seen on GB300: a 4-byte row received 16 bytes), so the row length must
     // be a multiple of 16 bytes as well as the pitch.
@@ -272,8 +302,12 @@ cudaError_t launch_fill_vd(int layout, void *states, size_t S, size_t m, size_t 
                                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r == CUDA_SUCCESS) {
-            k_fill_tma<V, DT><<<(unsigned)grid, FILL_WARPS * 32, FILL_SMEM, stream>>>(
-                map, states, S, m, write_back, status);
+            if (short_rows)
+                k_fill_tma<V, DT, true><<<(unsigned)tma_grid, CS::WARPS * 32, CS::SMEM, stream>>>(
+                    map, states, S, m, write_back, status);
+            else
+                k_fill_tma<V, DT, false><<<(unsigned)tma_grid, CL::WARPS * 32, CL::SMEM, stream>>>(
+                    map, states, S, m, write_back, status);
             count_launch();
             return cudaGetLastError();
         }
