@@ -312,9 +312,14 @@ typedef struct {
     int outputs_per_row, block;    /* batched kernel configuration; 0 = 16, 128 */
 } xr_server_config;
 
+/* Counters since creation.  For completed requests, summed over requests:
+ * queue_ns from submission to the start of its round's launch, launch_ns the
+ * host time launching that round (admission, plan upload, kernel launches),
+ * device_ns from the end of that launch to the observed completion. */
 typedef struct {
     uint64_t submitted, completed, released, rounds, bytes;
     uint64_t arena_in_use, arena_peak;
+    uint64_t queue_ns, launch_ns, device_ns;
 } xr_serve_stats;
 
 typedef struct xr_server xr_server;

@@ -50,7 +50,7 @@ class ServerConfig(ctypes.Structure):
 class ServeStats(ctypes.Structure):
     """xr_serve_stats of include/xr.h."""
     _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "completed", "released", "rounds", "bytes",
-                                                "arena_in_use", "arena_peak")]
+                                                "arena_in_use", "arena_peak", "queue_ns", "launch_ns", "device_ns")]
 
 
 class Request(ctypes.Structure):

@@ -444,7 +444,7 @@ static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 // from pinned memory.  Buffers grow (after waiting for `st`) only when a plan
 // is larger than any before; the pinned blob is reused, so the caller must
 // not upload again before this copy has completed.
-cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st)
+cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st, const void *extra, size_t extra_bytes)
 {
     d.off_reqs = 0;
     d.off_groups = up256(d.off_reqs + p.reqs.size() * sizeof(BReq));
@@ -452,7 +452,9 @@ cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st)
     d.off_prefix = up256(d.off_group_reqs + p.group_reqs.size() * sizeof(u32));
     d.off_tasks = up256(d.off_prefix + p.prefix.size() * sizeof(u64));
     d.off_items = up256(d.off_tasks + p.tasks.size() * sizeof(u64));
-    const size_t total = up256(d.off_items + p.items.size() * sizeof(BLevelItem)) + 256;
+    d.off_extra = up256(d.off_items + p.items.size() * sizeof(BLevelItem));
+    d.off_counter = up256(d.off_extra + extra_bytes);
+    const size_t total = d.off_counter + 256;
     cudaError_t err = cudaSuccess;
     if (total > d.blob_cap) {
         err = cudaStreamSynchronize(st);
@@ -489,6 +491,8 @@ cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st)
     put(d.off_prefix, p.prefix.data(), p.prefix.size() * sizeof(u64));
     put(d.off_tasks, p.tasks.data(), p.tasks.size() * sizeof(u64));
     put(d.off_items, p.items.data(), p.items.size() * sizeof(BLevelItem));
+    put(d.off_extra, extra, extra_bytes);
+    memset(d.pinned + d.off_counter, 0, sizeof(unsigned long long));
     return cudaMemcpyAsync(d.blob, d.pinned, total, cudaMemcpyHostToDevice, st);
 }
 
@@ -508,7 +512,7 @@ size_t batch_smem_bytes(int opt, int block) { return (size_t)(block / 32) * warp
 // segment-start levels, then the persistent fill.  `rows_bytes` is the size
 // of the output allocation the row tensor maps may cover.
 cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint64_t *d_seeds, void *d_slots,
-                         void *d_out, u64 rows_bytes, int opt, int block, cudaStream_t st)
+                         void *d_out, u64 rows_bytes, int opt, int block, cudaStream_t st, bool round_ready)
 {
     BatchDev d;
     d.reqs = (const BReq *)(dp.blob + dp.off_reqs);
@@ -518,7 +522,7 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
     d.tasks = (const u64 *)(dp.blob + dp.off_tasks);
     const BLevelItem *items = (const BLevelItem *)(dp.blob + dp.off_items);
     d.ntasks = p.tasks.size();
-    d.counter = dp.counter;
+    d.counter = round_ready ? reinterpret_cast<unsigned long long *>(dp.blob + dp.off_counter) : dp.counter;
     d.segstates = dp.segstates;
     d.slots = (unsigned char *)d_slots;
     d.out = (unsigned char *)d_out;
@@ -527,35 +531,45 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
     d.opt = opt;
     d.bufstride = bufstride_for(opt);
     d.warpbytes = warpbytes_for(opt);
-    CUtensorMap maps[2];
-    memset(maps, 0, sizeof(maps));
-    d.rows_ok = 0;
-    if (ctx->encode && d_out && ((uintptr_t)d_out % 16) == 0) {
-        d.rows_ok = 1;
-        for (int k = 0; k < 2; ++k) {
-            const u64 es = k == 0 ? 8 : 4, rows = rows_bytes / (BSEG * es);
-            if (rows == 0) continue;
-            if (rows >= (1ull << 31)) {
-                d.rows_ok = 0;
-                continue;
+    // tensor maps over the output as 1024-element rows: encoded again only
+    // when the output allocation changes
+    if (dp.maps_out != d_out || dp.maps_rows_bytes != rows_bytes) {
+        memset(dp.maps, 0, sizeof(dp.maps));
+        dp.maps_ok = 0;
+        if (ctx->encode && d_out && ((uintptr_t)d_out % 16) == 0) {
+            dp.maps_ok = 1;
+            for (int k = 0; k < 2; ++k) {
+                const u64 es = k == 0 ? 8 : 4, rows = rows_bytes / (BSEG * es);
+                if (rows == 0) continue;
+                if (rows >= (1ull << 31)) {
+                    dp.maps_ok = 0;
+                    continue;
+                }
+                const cuuint64_t dims[2] = {(cuuint64_t)BSEG, (cuuint64_t)rows};
+                const cuuint64_t strides[1] = {(cuuint64_t)(BSEG * es)};
+                const cuuint32_t box[2] = {(cuuint32_t)(128 / es), 32u};
+                const cuuint32_t estr[2] = {1u, 1u};
+                if (ctx->encode(&dp.maps[k], k == 0 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+                                2, d_out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                    dp.maps_ok = 0;
             }
-            const cuuint64_t dims[2] = {(cuuint64_t)BSEG, (cuuint64_t)rows};
-            const cuuint64_t strides[1] = {(cuuint64_t)(BSEG * es)};
-            const cuuint32_t box[2] = {(cuuint32_t)(128 / es), 32u};
-            const cuuint32_t estr[2] = {1u, 1u};
-            if (ctx->encode(&maps[k], k == 0 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2,
-                            d_out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-                d.rows_ok = 0;
         }
+        dp.maps_out = d_out;
+        dp.maps_rows_bytes = rows_bytes;
     }
+    d.rows_ok = dp.maps_ok;
     const size_t nreq = p.reqs.size();
-    cudaError_t err = cudaMemsetAsync(dp.counter, 0, sizeof(unsigned long long), st);
-    if (err != cudaSuccess || nreq == 0) return err;
-    k_batch_seed<<<(unsigned)((nreq + 127) / 128), 128, 0, st>>>(d, nreq);
-    count_launch();
-    err = cudaGetLastError();
+    if (nreq == 0) return cudaSuccess;
+    cudaError_t err = cudaSuccess;
+    if (!round_ready) {
+        err = cudaMemsetAsync(dp.counter, 0, sizeof(unsigned long long), st);
+        if (err != cudaSuccess) return err;
+        k_batch_seed<<<(unsigned)((nreq + 127) / 128), 128, 0, st>>>(d, nreq);
+        count_launch();
+        err = cudaGetLastError();
+    }
     for (size_t i = 0; i < p.levels.size() && err == cudaSuccess; ++i) {
         const LevelLaunch &L = p.levels[i];
         const int di = pset_index(L.engine, BSEG_LOG2);
@@ -578,15 +592,22 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
     static std::atomic<uint64_t> attr{0};
     err = set_smem_once(attr, k_batch_fill, 227 * 1024);
     if (err != cudaSuccess) return err;
-    int per_sm = 0, sms = 0;
     const size_t smem = batch_smem_bytes(opt, block);
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_fill, block, smem);
-    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    if (err != cudaSuccess) return err;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (dp.occ_opt != opt || dp.occ_block != block) {  // occupancy per configuration, once
+        int per_sm = 0, sms = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_fill, block, smem);
+        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        if (err != cudaSuccess) return err;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        dp.occ_opt = opt;
+        dp.occ_block = block;
+        dp.occ_per_sm = per_sm;
+        dp.occ_sms = sms;
+    }
     const u64 warps_per_block = (u64)block / 32;
-    const u64 grid = std::min<u64>((u64)per_sm * sms, (p.tasks.size() + warps_per_block - 1) / warps_per_block);
-    k_batch_fill<<<(unsigned)grid, block, smem, st>>>(d, maps[0], maps[1]);
+    const u64 grid = std::min<u64>((u64)dp.occ_per_sm * dp.occ_sms,
+                                   (p.tasks.size() + warps_per_block - 1) / warps_per_block);
+    k_batch_fill<<<(unsigned)grid, block, smem, st>>>(d, dp.maps[0], dp.maps[1]);
     count_launch();
     return cudaGetLastError();
 }

@@ -52,14 +52,29 @@ struct DevPlan {
     size_t seg_cap = 0;
     unsigned long long *counter = nullptr;
     size_t off_reqs = 0, off_groups = 0, off_group_reqs = 0, off_prefix = 0, off_tasks = 0, off_items = 0;
+    size_t off_extra = 0, off_counter = 0;  // caller's records; a task counter uploaded as zero
+    // launch facts reused while the output allocation and the configuration
+    // stay the same (a server runs every round on one arena)
+    CUtensorMap maps[2];
+    const void *maps_out = nullptr;
+    u64_t maps_rows_bytes = 0;
+    int maps_ok = 0;
+    int occ_opt = 0, occ_block = 0, occ_per_sm = 0, occ_sms = 0;
 };
 
 int check_requests(const xr_request *h, size_t nreq);
 void build_plan(const xr_request *in, size_t nreq, HostPlan &p);
-cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st);
+// `extra` (extra_bytes, may be empty) is copied into the blob at d.off_extra
+// with the plan, and a zeroed task counter at d.off_counter.
+cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st, const void *extra = nullptr,
+                        size_t extra_bytes = 0);
 void free_devplan(DevPlan &d);
 size_t batch_smem_bytes(int opt, int block);
+// round_ready: the plan was just uploaded (its counter is zero) and segment 0
+// of every request already holds the request's start state, so neither the
+// counter reset nor the seed step is enqueued.
 cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint64_t *d_seeds, void *d_slots,
-                         void *d_out, u64_t rows_bytes, int opt, int block, cudaStream_t st);
+                         void *d_out, u64_t rows_bytes, int opt, int block, cudaStream_t st,
+                         bool round_ready = false);
 
 }  // namespace xr

@@ -115,7 +115,9 @@ __device__ void warp_advance(const u32 *psets0, const u32 *tables, u32 (&v)[NW],
 }
 
 // One client's admitted requests in order, by one warp: each request gets the
-// current state in its slot, then the state advances by the request's n.
+// current state in its 32-byte destination (req.slot indexes `rslots`: a
+// round's segment states, at the request's first segment, or a plain slot),
+// then the state advances by the request's n.
 template <int NW>
 __device__ void admit_chain(const u32 *psets0, const u32 *tables, u32 *cstate, const AdmitReq *reqs, u32 first,
                             u32 count, unsigned char *rslots, int lane)
@@ -183,6 +185,7 @@ struct SReq {
     int dtype;
     u64 off, bytes;
     double t_sub, t_done;
+    double t_start = 0, t_launched = 0;  // round launch begun / enqueued (host clock)
     int state;
     bool auto_release;
 };
@@ -238,7 +241,7 @@ struct Round {
     std::vector<AdmitClient> aclients;
     std::vector<AdmitReq> areqs;
     unsigned char *d_slots = nullptr;
-    unsigned char *d_admit = nullptr, *h_admit = nullptr;
+    unsigned char *h_admit = nullptr;
     size_t admit_cap = 0;
     cudaStream_t st = nullptr;
     cudaEvent_t admitted = nullptr, done = nullptr;
@@ -312,6 +315,9 @@ static bool complete_finished(xr_server *s)
         SReq &q = s->reqs[tk];
         q.state = S_DONE;
         q.t_done = t;
+        s->stats.queue_ns += (u64)(1e3 * (q.t_start - q.t_sub));
+        s->stats.launch_ns += (u64)(1e3 * (q.t_launched - q.t_start));
+        s->stats.device_ns += (u64)(1e3 * (q.t_done - q.t_launched));
         s->stats.completed++;
         s->stats.bytes += q.n * (u64)es_of_dtype(q.dtype);
         if (q.auto_release) {
@@ -353,52 +359,51 @@ static bool complete_finished(xr_server *s)
 
 static cudaError_t launch_round(xr_server *s, Round &R)
 {
+    // The plan first: admission writes each request's start state straight
+    // into its first segment state (seg_base), so the round needs no seed step.
+    build_plan(R.reqs.data(), R.reqs.size(), R.plan);
     // admit arrays, grouped by client in submission order
     R.aclients.clear();
     R.areqs.clear();
-    std::map<u32, std::vector<u32>> byc;
-    for (u32 i = 0; i < (u32)R.reqs.size(); ++i) byc[R.clients[i]].push_back(i);
-    for (auto &kv : byc) {
+    std::vector<std::pair<u32, u32>> byc(R.reqs.size());  // (client, request)
+    for (u32 i = 0; i < (u32)R.reqs.size(); ++i) byc[i] = {R.clients[i], i};
+    std::stable_sort(byc.begin(), byc.end(),
+                     [](const std::pair<u32, u32> &x, const std::pair<u32, u32> &y) { return x.first < y.first; });
+    for (size_t k = 0; k < byc.size();) {
+        size_t e = k;
         AdmitClient c;
-        c.client = kv.first;
+        c.client = byc[k].first;
         c.first = (u32)R.areqs.size();
-        c.count = (u32)kv.second.size();
-        c.engine = (u32)engine_of(s->cvar[kv.first]);
+        c.engine = (u32)engine_of(s->cvar[c.client]);
+        for (; e < byc.size() && byc[e].first == c.client; ++e)
+            R.areqs.push_back({R.reqs[byc[e].second].n, R.plan.reqs[byc[e].second].seg_base});
+        c.count = (u32)(e - k);
         R.aclients.push_back(c);
-        for (u32 i : kv.second) R.areqs.push_back({R.reqs[i].n, (u64)i});
+        k = e;
     }
     const size_t ca = R.aclients.size() * sizeof(AdmitClient), ra = R.areqs.size() * sizeof(AdmitReq);
-    const size_t need = ((ca + 255) & ~(size_t)255) + ra + 256;
-    cudaError_t err = cudaSuccess;
-    if (need > R.admit_cap) {
-        err = cudaStreamSynchronize(s->admit_st);
-        cudaFree(R.d_admit);
-        cudaFreeHost(R.h_admit);
-        R.d_admit = R.h_admit = nullptr;
-        R.admit_cap = 0;
-        if (err == cudaSuccess) err = cudaMalloc((void **)&R.d_admit, need * 2);
-        if (err == cudaSuccess) err = cudaMallocHost((void **)&R.h_admit, need * 2);
-        if (err != cudaSuccess) return err;
-        R.admit_cap = need * 2;
-    }
     const size_t roff = (ca + 255) & ~(size_t)255;
+    if (roff + ra > R.admit_cap) return cudaErrorInvalidValue;  // sized for the largest round at creation
     memcpy(R.h_admit, R.aclients.data(), ca);
     memcpy(R.h_admit + roff, R.areqs.data(), ra);
-    err = cudaMemcpyAsync(R.d_admit, R.h_admit, roff + ra, cudaMemcpyHostToDevice, s->admit_st);
+    // plan + admission records + a zero task counter: one copy, on the
+    // admission stream, which orders the rounds' admissions
+    cudaError_t err = upload_plan(R.plan, R.dev, s->admit_st, R.h_admit, roff + ra);
     if (err != cudaSuccess) return err;
+    const unsigned char *recs = R.dev.blob + R.dev.off_extra;
     const u32 nc = (u32)R.aclients.size();
-    k_admit<<<(nc + 3) / 4, 128, 0, s->admit_st>>>(tables_of(s->ctx), steps_of(s->ctx), (const AdmitClient *)R.d_admit,
-                                                   nc, (const AdmitReq *)(R.d_admit + roff), s->d_cstates, R.d_slots);
+    k_admit<<<(nc + 3) / 4, 128, 0, s->admit_st>>>(tables_of(s->ctx), steps_of(s->ctx), (const AdmitClient *)recs,
+                                                   nc, (const AdmitReq *)(recs + roff), s->d_cstates,
+                                                   (unsigned char *)R.dev.segstates);
     count_launch();
     err = cudaGetLastError();
     if (err == cudaSuccess) err = cudaEventRecord(R.admitted, s->admit_st);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(R.st, R.admitted, 0);
-    build_plan(R.reqs.data(), R.reqs.size(), R.plan);
-    if (err == cudaSuccess) err = upload_plan(R.plan, R.dev, R.st);
     const int opt = s->cfg.outputs_per_row ? s->cfg.outputs_per_row : 16;
     const int block = s->cfg.block ? s->cfg.block : 128;
     if (err == cudaSuccess)
-        err = enqueue_plan(s->ctx, R.plan, R.dev, nullptr, R.d_slots, s->arena, s->cfg.arena_bytes, opt, block, R.st);
+        err = enqueue_plan(s->ctx, R.plan, R.dev, nullptr, R.d_slots, s->arena, s->cfg.arena_bytes, opt, block, R.st,
+                           true);
     if (err == cudaSuccess) err = cudaEventRecord(R.done, R.st);
     return err;
 }
@@ -462,9 +467,13 @@ static void scheduler(xr_server *s)
                     s->stats.rounds++;
                     s->stats.arena_in_use = s->alloc.in_use;
                     s->stats.arena_peak = s->alloc.peak;
+                    const double t_start = now_us();
+                    for (u64 tk : R.tickets) s->reqs[tk].t_start = t_start;
                     lk.unlock();
                     const cudaError_t err = launch_round(s, R);
+                    const double t_launched = now_us();
                     lk.lock();
+                    for (u64 tk : R.tickets) s->reqs[tk].t_launched = t_launched;
                     if (err != cudaSuccess) s->error = sst(err);
                     s->inflight.push_back(ri);
                     progress = true;
@@ -484,10 +493,13 @@ static void scheduler(xr_server *s)
                 s->stats.arena_in_use = s->alloc.in_use;
                 s->stats.arena_peak = s->alloc.peak;
                 const int slot = (int)(plain_seq++ % PLAIN_DEPTH);
+                q.t_start = now_us();
                 const SReq qc = q;
                 lk.unlock();
                 const cudaError_t err = launch_plain(s, qc, ev, slot);
+                const double t_launched = now_us();
                 lk.lock();
+                s->reqs[tk].t_launched = t_launched;
                 if (err != cudaSuccess) s->error = sst(err);
                 s->plain_inflight.push_back({tk, ev});
                 progress = true;
@@ -522,7 +534,6 @@ extern "C" int xr_server_destroy(xr_server *s)
     for (Round &R : s->rounds) {
         free_devplan(R.dev);
         cudaFree(R.d_slots);
-        cudaFree(R.d_admit);
         cudaFreeHost(R.h_admit);
         if (R.st) cudaStreamDestroy(R.st);
         if (R.admitted) cudaEventDestroy(R.admitted);
@@ -588,13 +599,13 @@ extern "C" int xr_server_create(xr_ctx *ctx, const xr_server_config *cfg, const 
             if (err == cudaSuccess) err = cudaEventCreateWithFlags(&R.admitted, cudaEventDisableTiming);
             if (err == cudaSuccess) err = cudaEventCreateWithFlags(&R.done, cudaEventDisableTiming);
             if (err == cudaSuccess) err = cudaMalloc((void **)&R.d_slots, (size_t)cfg->max_round_requests * 32);
-            // admission records for the largest round (a round has at most as
-            // many clients as requests), so no round reallocates them
+            // host staging of the admission records for the largest round (a
+            // round has at most as many clients as requests); they travel to
+            // the device inside the plan upload
             if (err == cudaSuccess) {
                 const size_t ca = (size_t)cfg->max_round_requests * sizeof(AdmitClient);
                 R.admit_cap = ((ca + 255) & ~(size_t)255) + (size_t)cfg->max_round_requests * sizeof(AdmitReq) + 256;
-                err = cudaMalloc((void **)&R.d_admit, R.admit_cap);
-                if (err == cudaSuccess) err = cudaMallocHost((void **)&R.h_admit, R.admit_cap);
+                err = cudaMallocHost((void **)&R.h_admit, R.admit_cap);
             }
             // size the plan buffers for the largest round up front
             if (err == cudaSuccess) {
@@ -602,7 +613,7 @@ extern "C" int xr_server_create(xr_ctx *ctx, const xr_server_config *cfg, const 
                 err = cudaMalloc((void **)&R.dev.segstates, R.dev.seg_cap);
             }
             if (err == cudaSuccess) {
-                R.dev.blob_cap = (size_t)cfg->max_round_requests * 160 + segcap / 32 * 8 * 2 + (1 << 20);
+                R.dev.blob_cap = (size_t)cfg->max_round_requests * 160 + segcap / 32 * 8 * 2 + R.admit_cap + (1 << 20);
                 err = cudaMalloc((void **)&R.dev.blob, R.dev.blob_cap);
                 if (err == cudaSuccess) err = cudaMallocHost((void **)&R.dev.pinned, R.dev.blob_cap);
             }
