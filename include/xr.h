@@ -309,7 +309,7 @@ typedef struct {
     uint32_t max_rounds;           /* rounds in flight (batched mode), >= 1 */
     uint32_t max_round_requests;   /* requests per round (batched mode), >= 1 */
     int mode;                      /* XR_SERVE_BATCHED or XR_SERVE_PLAIN */
-    int outputs_per_row, block;    /* batched kernel configuration; 0 = 16, 128 */
+    int outputs_per_row, block;    /* batched kernel configuration; 0 = 32, 128 */
 } xr_server_config;
 
 /* Counters since creation.  For completed requests, summed over requests:

@@ -98,7 +98,9 @@ __global__ void k_batch_seed(BatchDev d, size_t nreq)
 // One level of the power-set scheme over many requests of one engine:
 // segstates[parent + j * stride] = P[j] segstates[parent] when inside the
 // request (below `limit`).  The CTA shares j, builds the Four-Russians tables
-// of P[j] in shared memory and handles two items per thread.
+// of P[j] in shared memory and handles two items per thread.  Items come
+// longest first, so a CTA whose first item has no child j has nothing to do
+// and leaves before building its tables.
 constexpr int BLEVEL_ITEMS_PER_THREAD = 2;
 
 template <int NW>
@@ -109,6 +111,10 @@ __global__ void __launch_bounds__(256)
     typedef Russians<NW> RT;
     __shared__ __align__(16) u32 T[RT::WORDS];
     const int j = blockIdx.y + 1;
+    {
+        const BLevelItem lead = items[(size_t)blockIdx.x * BLEVEL_ITEMS_PER_THREAD * blockDim.x];
+        if (lead.parent + (u64)j * stride >= lead.limit) return;
+    }
     russians_build<NW>(P + (size_t)j * RT::n * NW, T);
     __syncthreads();
 #pragma unroll
@@ -201,23 +207,40 @@ __device__ __forceinline__ void batch_lane(const u32 *st, unsigned char *slot, u
     if (slot) store_state(e, slot);
 }
 
+// Wait until at most n (1..7) committed bulk groups still read shared memory;
+// the count must be an immediate, so each depth has its own instruction.
+__device__ __forceinline__ void bulk_wait_read_n(int n)
+{
+    switch (n) {
+    case 1: bulk_wait_read<1>(); break;
+    case 2: bulk_wait_read<2>(); break;
+    case 3: bulk_wait_read<3>(); break;
+    case 4: bulk_wait_read<4>(); break;
+    case 5: bulk_wait_read<5>(); break;
+    case 6: bulk_wait_read<6>(); break;
+    default: bulk_wait_read<7>(); break;
+    }
+}
+
 // A warp whose 32 lanes hold 32 consecutive full segments of one request:
 // the segments are 32 consecutive 1024-element rows of the arena, written as
 // 32-row x 128-byte tiles by 2D TMA stores, exactly like the bulk fill.
+// `ntiles` (2..8) tiles rotate, so up to ntiles stores are in flight.
 template <int V, int DT>
 __device__ __forceinline__ void batch_warp_rows(const u32 *st, unsigned char *slot, const CUtensorMap *map,
-                                                int row0, u32 tiles, int lane)
+                                                int row0, u32 tiles, int ntiles, int lane)
 {
     typedef Gen<V> G;
     typedef typename G::E E;
     constexpr int COLS = 128 / (int)sizeof(typename OutElem<DT>::type);
     E e;
     load_state(e, st);
-    int it = 0;
+    int it = 0, k = 0;
     for (int j0 = 0; j0 < (int)BSEG; j0 += COLS, ++it) {
-        const u32 tile = tiles + (u32)((it & 1) * TILE_BYTES_B);
-        if (it >= 2) {
-            if (lane == 0) bulk_wait_read<1>();
+        const u32 tile = tiles + (u32)(k * TILE_BYTES_B);
+        k = k + 1 == ntiles ? 0 : k + 1;
+        if (it >= ntiles) {
+            if (lane == 0) bulk_wait_read_n(ntiles - 1);
             __syncwarp();
         }
         fill_tile_row<G, DT>(e, tile, lane, (size_t)COLS, true, st, (size_t)j0);  // st is read only here
@@ -235,7 +258,7 @@ __device__ __forceinline__ void batch_warp_rows(const u32 *st, unsigned char *sl
 
 #define XR_BATCH_CASE(V, DT)                                                              \
     case (V) * 4 + (DT):                                                                  \
-        if (full) batch_warp_rows<V, DT>(st, slot, (DT == DT_U32 || DT == DT_F32) ? &map32 : &map64, row0, tiles, lane); \
+        if (full) batch_warp_rows<V, DT>(st, slot, (DT == DT_U32 || DT == DT_F32) ? &map32 : &map64, row0, tiles, ntiles, lane); \
         else batch_lane<V, DT>(st, slot, out, count, buf0, bufnext, d.opt);               \
         break;
 
@@ -245,7 +268,9 @@ __global__ void __launch_bounds__(512)
     extern __shared__ unsigned char bsmem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const u32 wbase = ((smem_addr(bsmem) + 1023u) & ~1023u) + (u32)warp * d.warpbytes;
-    const u32 tiles = wbase;                       // two 4 KiB tiles (full tasks)
+    const u32 tiles = wbase;                       // 4 KiB tiles (full tasks)
+    // full tasks rotate as many tiles as the warp's share holds (at most 8)
+    const int ntiles = (int)min(8u, d.warpbytes / (u32)TILE_BYTES_B);
     const u32 buf0 = wbase + (u32)lane * d.bufstride;  // per-lane rows (other tasks)
     const u32 bufnext = 32u * d.bufstride;
     for (;;) {
@@ -424,7 +449,13 @@ void build_plan(const xr_request *in, size_t nreq, HostPlan &p)
                     p.items.push_back({p.reqs[r].seg_base + k * span, p.reqs[r].seg_base + P});
             }
             L.count = p.items.size() - L.first;
-            if (L.count) p.levels.push_back(L);
+            if (!L.count) continue;
+            std::sort(p.items.begin() + L.first, p.items.end(), [](const BLevelItem &a, const BLevelItem &b) {
+                return a.limit - a.parent > b.limit - b.parent;
+            });
+            const u64 kids = (p.items[L.first].limit - p.items[L.first].parent + stride - 1) / stride;
+            L.maxj = (unsigned)std::min<u64>(kids - 1, PSET_SIZE - 1);
+            p.levels.push_back(L);
         }
     }
 }
@@ -498,7 +529,8 @@ cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st, const vo
 
 static u32 bufstride_for(int opt) { return (u32)(opt * 8 + 16); }
 // Per warp: two 32 x 128-byte tiles (full tasks) or 32 lanes x two staged
-// rows (other tasks), whichever is larger, in 1024-byte units.
+// rows (other tasks), whichever is larger, in 1024-byte units.  Full tasks
+// then rotate as many tiles as that share holds.
 static u32 warpbytes_for(int opt)
 {
     const u32 rows = (u32)BATCH_NBUF * 32u * bufstride_for(opt);
@@ -577,7 +609,7 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
         const size_t set_words = (size_t)PSET_SIZE * n * (n / 32);
         const uint32_t *P = pset_sets(ctx, L.engine, di) + (size_t)L.level * set_words;
         const size_t per_cta = (size_t)256 * BLEVEL_ITEMS_PER_THREAD;
-        const dim3 grid((unsigned)((L.count + per_cta - 1) / per_cta), PSET_SIZE - 1);
+        const dim3 grid((unsigned)((L.count + per_cta - 1) / per_cta), L.maxj);
         const u64 stride = 1ull << (PSET_BITS * L.level);
         if (n == 256)
             k_batch_level<8><<<grid, 256, 0, st>>>(P, items + L.first, L.count, stride, dp.segstates);

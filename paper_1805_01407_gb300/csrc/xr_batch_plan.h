@@ -26,9 +26,12 @@ struct BLevelItem {
     u64_t parent, limit;  // parent segment index (absolute) and end of its request's segments
 };
 
+// Items of one launch are sorted by the segments they span, longest first;
+// maxj is the largest power-set index any of them uses.
 struct LevelLaunch {
     int engine, level;
     size_t first, count;
+    unsigned int maxj;
 };
 
 struct HostPlan {

@@ -400,65 +400,97 @@ __device__ __forceinline__ void f2_matvec(const u32 *__restrict__ M, const u32 (
 }
 
 // Four-Russians tables of one F2 matrix (n columns of NW words): for each
-// group of three consecutive columns 3g .. 3g+2, the XOR of every subset (8
-// entries), so a matrix-vector product is n/3 table reads instead of n
-// masked XORs.  An entry is split into 16-byte pieces (8-byte for NW = 2);
-// piece h of the 8 entries of a group is stored contiguously (128 or 64
-// bytes), so any lanes of a quarter-warp (half-warp) reading entries of one
-// group hit distinct banks.
+// group of four consecutive columns 4g .. 4g+3, the XOR of every subset (16
+// entries), so a matrix-vector product is n/4 table reads instead of n
+// masked XORs.  An entry is split into 16-byte pieces (8-byte for NW = 2).
+// Piece h of entry e of group g sits at slot (e H + h) G + g, so the bank of
+// a read depends on the group alone; lane l visits the groups in the order
+// l, l+1, ... (mod G), which puts the 8 lanes of a quarter-warp (16 of a
+// half-warp for 8-byte pieces) on distinct banks whatever their entries.
 template <int NW>
 struct Russians {
     static constexpr int n = NW * 32;
-    static constexpr int G = (n + 2) / 3;       // groups of three columns
+    static constexpr int G = n / 4;             // groups of four columns
     static constexpr int Q = NW >= 4 ? 4 : NW;  // words per piece
     static constexpr int H = NW / Q;            // pieces per entry
-    static constexpr int WORDS = G * 8 * NW;
+    static constexpr int WORDS = 16 * G * NW;
 };
 
+// Thread task (h, g, q) builds word q of piece h for the 16 entries of group
+// g, each from a smaller entry and one column: T[e] = T[e - b] ^ col(4g + k)
+// for b = 2^k the top bit of e.  The matrix is read once.
 template <int NW>
 __device__ __forceinline__ void russians_build(const u32 *__restrict__ M, u32 *T)
 {
     typedef Russians<NW> RT;
-    for (int i = threadIdx.x; i < RT::WORDS; i += blockDim.x) {
-        const int q = i % RT::Q, e = (i / RT::Q) % 8, gh = i / (RT::Q * 8);
-        const int h = gh % RT::H, g = gh / RT::H;
+    for (int i = threadIdx.x; i < RT::G * NW; i += blockDim.x) {
+        const int q = i % RT::Q, g = (i / RT::Q) % RT::G, h = i / (RT::Q * RT::G);
         const int word = h * RT::Q + q;
-        u32 x = 0u;
+        u32 c[4];
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const int col = 3 * g + b;
-            if (((e >> b) & 1) && col < RT::n) x ^= __ldg(M + (size_t)col * NW + word);
+        for (int k = 0; k < 4; ++k) c[k] = __ldg(M + (size_t)(4 * g + k) * NW + word);
+        u32 x[16];
+        x[0] = 0u;
+#pragma unroll
+        for (int e = 1; e < 16; ++e) {
+            const int k = e >= 8 ? 3 : (e >= 4 ? 2 : (e >= 2 ? 1 : 0));
+            x[e] = x[e - (1 << k)] ^ c[k];
         }
-        T[i] = x;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) T[((e * RT::H + h) * RT::G + g) * RT::Q + q] = x[e];
     }
 }
 
+// r = M v from the tables.  The vector is first rotated right by 4 lane bits
+// (mod n), so step s reads the fixed bits 4s .. 4s+3 of the rotated vector,
+// which are group (s + lane) mod G of v.
 template <int NW>
 __device__ __forceinline__ void russians_matvec(const u32 *T, const u32 (&v)[NW], u32 (&r)[NW])
 {
     typedef Russians<NW> RT;
+    const int lane = (int)(threadIdx.x & 31u);
+    const int rot = (4 * lane) & (RT::n - 1);  // bits; below 128
+    u32 u[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) u[w] = v[w];
+    // whole words first (1 and 2 words), then the bits within a word
+#pragma unroll
+    for (int st = 1; st <= 2; st <<= 1) {
+        if (st < NW && ((rot >> 5) & st)) {
+            u32 t[NW];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) t[w] = u[(w + st) % NW];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) u[w] = t[w];
+        }
+    }
+    const int bs = rot & 31;
+    {
+        u32 t[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) t[w] = __funnelshift_r(u[w], u[(w + 1) % NW], bs);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) u[w] = t[w];
+    }
 #pragma unroll
     for (int w = 0; w < NW; ++w) r[w] = 0u;
 #pragma unroll
-    for (int g = 0; g < RT::G; ++g) {
-        const int bit = 3 * g, w = bit >> 5, sh = bit & 31;
-        u32 e;
-        if (sh <= 29 || w + 1 >= NW) e = (v[w] >> sh) & 7u;
-        else e = __funnelshift_r(v[w], v[w + 1], sh) & 7u;
+    for (int s = 0; s < RT::G; ++s) {
+        const u32 e = (u[(4 * s) >> 5] >> ((4 * s) & 31)) & 15u;
+        const u32 g = (u32)(s + lane) & (u32)(RT::G - 1);
 #pragma unroll
         for (int h = 0; h < RT::H; ++h) {
-            const u32 *piece = T + ((g * RT::H + h) * 8) * RT::Q + e * RT::Q;
+            const u32 slot = (e * RT::H + (u32)h) * RT::G + g;
             if constexpr (RT::Q == 4) {
-                const uint4 t = *reinterpret_cast<const uint4 *>(piece);
+                const uint4 t = reinterpret_cast<const uint4 *>(T)[slot];
                 r[4 * h] ^= t.x; r[4 * h + 1] ^= t.y; r[4 * h + 2] ^= t.z; r[4 * h + 3] ^= t.w;
             } else {
-                const uint2 t = *reinterpret_cast<const uint2 *>(piece);
+                const uint2 t = reinterpret_cast<const uint2 *>(T)[slot];
                 r[0] ^= t.x; r[1] ^= t.y;
             }
         }
     }
 }
-
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ u32 smem_addr(const void *p)

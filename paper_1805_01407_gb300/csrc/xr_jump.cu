@@ -7,6 +7,8 @@
 // steps multiplies by T^(2^(d+b)) for each set bit b of e; start states of
 // consecutive streams come from a doubling tree, one matrix-vector product per
 // stream: x_{2^L + i} = T^(2^(d+L)) x_i.
+#include <algorithm>
+
 #include "xr_device.cuh"
 #include "xr_internal.h"
 
@@ -385,7 +387,9 @@ cudaError_t launch_streams_psets(int engine, const uint32_t *sets3, void *states
         const size_t span = stride * PSET_SIZE;
         const size_t nparents = (S + span - 1) / span;
         const size_t per_cta = (size_t)256 * STREAMS_PER_THREAD;
-        const dim3 grid((unsigned)((nparents + per_cta - 1) / per_cta), PSET_SIZE - 1);
+        // children j of parent 0 stop below S (only the top level has fewer than 511)
+        const size_t maxj = std::min<size_t>(PSET_SIZE - 1, (S + stride - 1) / stride - 1);
+        const dim3 grid((unsigned)((nparents + per_cta - 1) / per_cta), (unsigned)maxj);
         const uint32_t *P = sets3 + (size_t)l * set_words;
         if (n == 256) k_streams_level<8><<<grid, 256, 0, stream>>>(P, (u32 *)states, S, stride, nparents);
         else if (n == 128) k_streams_level<4><<<grid, 256, 0, stream>>>(P, (u32 *)states, S, stride, nparents);

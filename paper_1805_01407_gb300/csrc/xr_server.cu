@@ -399,7 +399,7 @@ static cudaError_t launch_round(xr_server *s, Round &R)
     err = cudaGetLastError();
     if (err == cudaSuccess) err = cudaEventRecord(R.admitted, s->admit_st);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(R.st, R.admitted, 0);
-    const int opt = s->cfg.outputs_per_row ? s->cfg.outputs_per_row : 16;
+    const int opt = s->cfg.outputs_per_row ? s->cfg.outputs_per_row : 32;
     const int block = s->cfg.block ? s->cfg.block : 128;
     if (err == cudaSuccess)
         err = enqueue_plan(s->ctx, R.plan, R.dev, nullptr, R.d_slots, s->arena, s->cfg.arena_bytes, opt, block, R.st,
