@@ -124,14 +124,29 @@ __global__ void __launch_bounds__(256)
         const BLevelItem it = items[idx];
         const u64 child = it.parent + (u64)j * stride;
         if (child >= it.limit) continue;
+        // 32-byte slots: whole 16-byte loads and stores (the unused words of a
+        // slot are written as zero)
         u32 v[NW], r[NW];
-        const u32 *ps = segstates + it.parent * SLOT_WORDS;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) v[w] = ps[w];
+        const uint4 *ps = reinterpret_cast<const uint4 *>(segstates + it.parent * SLOT_WORDS);
+        const uint4 a = ps[0];
+        v[0] = a.x; v[1] = a.y;
+        if constexpr (NW >= 4) { v[2] = a.z; v[3] = a.w; }
+        if constexpr (NW == 8) {
+            const uint4 b = ps[1];
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        }
         russians_matvec<NW>(T, v, r);
-        u32 *cs = segstates + child * SLOT_WORDS;
-#pragma unroll
-        for (int w = 0; w < SLOT_WORDS; ++w) cs[w] = w < NW ? r[w % NW] : 0u;
+        uint4 *cs = reinterpret_cast<uint4 *>(segstates + child * SLOT_WORDS);
+        if constexpr (NW == 8) {
+            cs[0] = make_uint4(r[0], r[1], r[2], r[3]);
+            cs[1] = make_uint4(r[4], r[5], r[6], r[7]);
+        } else if constexpr (NW == 4) {
+            cs[0] = make_uint4(r[0], r[1], r[2], r[3]);
+            cs[1] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+            cs[0] = make_uint4(r[0], r[1], 0u, 0u);
+            cs[1] = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
 }
 
