@@ -238,6 +238,29 @@ def cpu_baseline(seconds):
             "seconds": t, "bytes": b}
 
 
+def _oracle_worker(task):
+    streams, m, seed = task
+    return oracle_sample(streams, m, seed)
+
+
+def cpu_baseline_all_cores(streams):
+    """The same oracle sample once per host core, in spawned processes started
+    together (one single-threaded oracle each): aggregate bytes / wall time."""
+    import multiprocessing as mp
+    m, seed = W.CONFIG_BULK["m"], W.CONFIG_BULK["seed"]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_worker, [(1, m, seed)] * cores, chunksize=1)  # every process loads the oracle
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [(streams, m, seed)] * cores, chunksize=1)
+        wall = time.perf_counter() - t0
+    b = sum(r[0] for r in res)
+    return {"value": b / wall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d processes, each the single-threaded plain C oracle on 16 jobs x %d streams x %d outputs "
+                      "(the cpu_baseline recipe), started together; %.1f s wall" % (cores, streams, m, wall),
+            "seconds": wall, "bytes": b}
+
+
 def extra_cpu_baseline(streams=64):
     """The oracle on the other generators of the paper, the same recipe as the
     extra-generator leg (SplitMix64(42) base, streams J^i, 2^10 outputs each,
@@ -437,6 +460,8 @@ def run_xr(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(
+            max(64, line["cpu_baseline"]["bytes"] // (16 * 8 * W.CONFIG_BULK["m"]) // 4))
     if not args.no_batched:
         line["batched"] = run_batched(xr, ctx, args)
     if not args.no_serve:
@@ -625,8 +650,9 @@ def run_analysis(xr, ctx, args):
 def run_jumpstart(xr, ctx, args):
     """Jump-start at scale: 2^24 xoshiro256++ streams J^i(s0) and L^i(s0) from
     SplitMix64(42), then 64 u64 outputs each; stream starts and fill timed
-    with events on their stream (median of 3).  A stream start is one 256 x
-    256 F2 matrix-vector product (three power-set levels)."""
+    with events on their stream (median of 3), then both pipelined over 16
+    chunks on two streams.  A stream start is one 256 x 256 F2
+    matrix-vector product (three power-set levels)."""
     import torch
     c = W.CONFIG_JUMPSTART
     v, S, m = c["variant"], c["S"], c["m"]
@@ -648,14 +674,38 @@ def run_jumpstart(xr, ctx, args):
             ts.append(a.elapsed_time(b))
         return statistics.median(ts)
 
+    # Pipelined: the streams in 16 chunks; the starts of chunk c+1 (side stream,
+    # higher priority) overlap the fill of chunk c (main stream), through the
+    # same public calls with first = c * S / 16.
+    chunks = 16
+    cs = S // chunks
+    sb = len(states) // S
+    side = torch.cuda.Stream(priority=-1)
+    ready = [torch.cuda.Event() for _ in range(chunks)]
+
+    def pipelined(kind):
+        side.wait_stream(stream)
+        for k in range(chunks):
+            ctx.make_streams(v, kind, base, k * cs, cs, states[k * cs * sb:(k + 1) * cs * sb], stream=side)
+            ready[k].record(side)
+        for k in range(chunks):
+            stream.wait_event(ready[k])
+            ctx.fill(v, states[k * cs * sb:(k + 1) * cs * sb], cs, m, "u64", out[k * cs * m:(k + 1) * cs * m],
+                     stream=stream)
+
     res = {"workload": "%s, %d streams x %d u64 outputs, SplitMix64(%d) base" % (v, S, m, c["seed"])}
     for kind in c["kinds"]:
         ms_streams = timed(lambda: ctx.make_streams(v, kind, base, 0, S, states))
         ms_fill = timed(lambda: ctx.fill(v, states, S, m, "u64", out))
+        check = int(out.view(torch.int64).sum())
+        ms_pipe = timed(lambda: pipelined(kind))
+        same = int(out.view(torch.int64).sum()) == check
         res[kind] = {"streams_ms": ms_streams, "streams_per_s": S / (ms_streams / 1e3),
                      "fill_ms": ms_fill, "fill_gbs": S * m * 8 / (ms_fill / 1e3) / 1e9,
                      "fill_frac_of_measured_peak": S * m * 8 / (ms_fill / 1e3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
-                     "total_gbs": S * m * 8 / ((ms_streams + ms_fill) / 1e3) / 1e9}
+                     "total_gbs": S * m * 8 / ((ms_streams + ms_fill) / 1e3) / 1e9,
+                     "pipelined_ms": ms_pipe, "pipelined_gbs": S * m * 8 / (ms_pipe / 1e3) / 1e9,
+                     "pipelined_chunks": chunks, "pipelined_same_output": same}
     del out, states
     torch.cuda.synchronize()
     assert ctx.status() == 0

@@ -409,14 +409,17 @@ static cudaError_t make_streams(xr_ctx *ctx, int variant, int d, const void *d_b
 {
     if (S == 0) return cudaSuccess;
     const int e = engine_of(variant);
-    cudaError_t err = cudaMemcpyAsync(out, d_base, (size_t)xr_state_bytes(variant),
-                                      cudaMemcpyDeviceToDevice, st);
-    if (err != cudaSuccess) return err;
-    if (first) {
-        err = launch_apply_pow(e, ctx->tables[e], klist(first, d, engine_bits(e)), out, 1, st);
-        if (err != cudaSuccess) return err;
-    }
     const int di = pset_index(e, d);
+    cudaError_t err;
+    if (first && di >= 0) {
+        // J^first(base) by one warp from the power sets of this distance
+        err = launch_warp_jump(e, pset_sets(ctx, e, di), ctx->tables[e], d, d_base, out, first, st);
+    } else {
+        err = cudaMemcpyAsync(out, d_base, (size_t)xr_state_bytes(variant), cudaMemcpyDeviceToDevice, st);
+        if (err == cudaSuccess && first)
+            err = launch_apply_pow(e, ctx->tables[e], klist(first, d, engine_bits(e)), out, 1, st);
+    }
+    if (err != cudaSuccess) return err;
     if (di >= 0 && S <= ((size_t)1 << (PSET_BITS * PSET_LEVELS)))
         return launch_streams_psets(e, pset_sets(ctx, e, di), out, S, st);
     return launch_tree(e, ctx->tables[e], d, out, S, st);

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "xr_internal.h"
+
 namespace xr {
 
 typedef unsigned long long u64;
@@ -489,6 +491,63 @@ __device__ __forceinline__ void russians_matvec(const u32 *T, const u32 (&v)[NW]
                 r[0] ^= t.x; r[1] ^= t.y;
             }
         }
+    }
+}
+
+// r = M v by one warp for a warp-uniform v: lane l owns columns k*32 + l, so
+// the column loads of the warp are contiguous, and the partial sums are
+// XOR-reduced across the lanes.
+template <int NW>
+__device__ __forceinline__ void warp_matvec(const u32 *__restrict__ M, u32 (&v)[NW], int lane)
+{
+    u32 acc[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) acc[w] = 0u;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        const u32 mask = 0u - ((v[k] >> lane) & 1u);
+        const u32 *colp = M + (size_t)(k * 32 + lane) * NW;
+        if constexpr (NW >= 4) {
+            const uint4 *col = reinterpret_cast<const uint4 *>(colp);
+#pragma unroll
+            for (int q = 0; q < NW / 4; ++q) {
+                const uint4 c = __ldg(col + q);
+                acc[4 * q] ^= c.x & mask;
+                acc[4 * q + 1] ^= c.y & mask;
+                acc[4 * q + 2] ^= c.z & mask;
+                acc[4 * q + 3] ^= c.w & mask;
+            }
+        } else {
+            const uint2 c = __ldg(reinterpret_cast<const uint2 *>(colp));
+            acc[0] ^= c.x & mask;
+            acc[1] ^= c.y & mask;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1)
+#pragma unroll
+        for (int w = 0; w < NW; ++w) acc[w] ^= __shfl_xor_sync(0xffffffffu, acc[w], off);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) v[w] = acc[w];
+}
+
+// v <- (T^(2^d))^e v by one warp, with psets_d the three power sets of the
+// distance 2^d (P_l[j] = T^(2^d j 512^l)): the low 27 bits of e take three
+// products at most, higher bits one T^(2^(d + k)) each (exponents mod n).
+template <int NW>
+__device__ void warp_advance(const u32 *psets_d, const u32 *tables, int d, u32 (&v)[NW], u64 e, int lane)
+{
+    constexpr int n = NW * 32;
+    const size_t set_words = (size_t)PSET_SIZE * n * NW;
+    for (int l = 0; l < PSET_LEVELS; ++l) {
+        const u32 j = (u32)(e >> (PSET_BITS * l)) & (PSET_SIZE - 1);
+        if (j) warp_matvec<NW>(psets_d + l * set_words + (size_t)j * n * NW, v, lane);
+    }
+    u64 hi = e >> (PSET_BITS * PSET_LEVELS);
+    while (hi) {
+        const int k = __ffsll((long long)hi) - 1;
+        hi &= hi - 1;
+        warp_matvec<NW>(tables + (size_t)((d + PSET_BITS * PSET_LEVELS + k) % n) * n * NW, v, lane);
     }
 }
 

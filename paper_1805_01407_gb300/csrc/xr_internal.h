@@ -65,6 +65,10 @@ cudaError_t launch_build_power_sets(int engine, const uint32_t *tables, const in
 // with states[i] = (T^(2^d))^i states[0], sets3 = the three sets of distance d.
 cudaError_t launch_streams_psets(int engine, const uint32_t *sets3, void *states, size_t S,
                                  cudaStream_t stream);
+// out = (T^(2^d))^e base by one warp through the three power sets of distance
+// 2^d (engines with power sets only: 256, 128 or 64 state bits).
+cudaError_t launch_warp_jump(int engine, const uint32_t *psets_d, const uint32_t *tables, int d, const void *base,
+                             void *out, uint64_t e, cudaStream_t stream);
 
 // SplitMix64 seeding: count states from d_seeds (or from `seed` when d_seeds
 // is NULL and count == 1).

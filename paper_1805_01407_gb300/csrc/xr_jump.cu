@@ -181,6 +181,34 @@ cudaError_t launch_apply_pow(int engine, const uint32_t *tables, const KList &ks
     return cudaGetLastError();
 }
 
+// out = (T^(2^d))^e base by one warp: the start state of a range of streams
+// that does not begin at stream 0.
+template <int NW>
+__global__ void __launch_bounds__(32)
+    k_warp_jump(const u32 *__restrict__ psets_d, const u32 *__restrict__ tables, int d, const u32 *base, u32 *out,
+                u64 e)
+{
+    const int lane = threadIdx.x;
+    u32 v[NW];
+    load_vec<NW>(v, base);
+    warp_advance<NW>(psets_d, tables, d, v, e, lane);
+    if (lane == 0) store_vec<NW>(v, out);
+}
+
+cudaError_t launch_warp_jump(int engine, const uint32_t *psets_d, const uint32_t *tables, int d, const void *base,
+                             void *out, uint64_t e, cudaStream_t stream)
+{
+    const u32 *P = (const u32 *)psets_d, *T = (const u32 *)tables, *b = (const u32 *)base;
+    switch (engine_bits(engine)) {
+    case 256: k_warp_jump<8><<<1, 32, 0, stream>>>(P, T, d, b, (u32 *)out, e); break;
+    case 128: k_warp_jump<4><<<1, 32, 0, stream>>>(P, T, d, b, (u32 *)out, e); break;
+    case 64: k_warp_jump<2><<<1, 32, 0, stream>>>(P, T, d, b, (u32 *)out, e); break;
+    default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- doubling tree
 
 // Levels L while 2^L < min(S, 2 * blockDim): one CTA, the level matrix staged

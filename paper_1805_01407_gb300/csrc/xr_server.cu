@@ -58,62 +58,6 @@ __global__ void k_server_seed(const int *variants, const u64 *seeds, u32 nclient
     d[1] = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
-// r = M v by one warp for a warp-uniform v: lane l owns columns k*32 + l, so
-// the column loads of the warp are contiguous, and the partial sums are
-// XOR-reduced across the lanes.
-template <int NW>
-__device__ __forceinline__ void warp_matvec(const u32 *__restrict__ M, u32 (&v)[NW], int lane)
-{
-    u32 acc[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) acc[w] = 0u;
-#pragma unroll
-    for (int k = 0; k < NW; ++k) {
-        const u32 mask = 0u - ((v[k] >> lane) & 1u);
-        const u32 *colp = M + (size_t)(k * 32 + lane) * NW;
-        if constexpr (NW >= 4) {
-            const uint4 *col = reinterpret_cast<const uint4 *>(colp);
-#pragma unroll
-            for (int q = 0; q < NW / 4; ++q) {
-                const uint4 c = __ldg(col + q);
-                acc[4 * q] ^= c.x & mask;
-                acc[4 * q + 1] ^= c.y & mask;
-                acc[4 * q + 2] ^= c.z & mask;
-                acc[4 * q + 3] ^= c.w & mask;
-            }
-        } else {
-            const uint2 c = __ldg(reinterpret_cast<const uint2 *>(colp));
-            acc[0] ^= c.x & mask;
-            acc[1] ^= c.y & mask;
-        }
-    }
-#pragma unroll
-    for (int off = 16; off; off >>= 1)
-#pragma unroll
-        for (int w = 0; w < NW; ++w) acc[w] ^= __shfl_xor_sync(0xffffffffu, acc[w], off);
-#pragma unroll
-    for (int w = 0; w < NW; ++w) v[w] = acc[w];
-}
-
-// v <- T^e v: the low 27 bits of e through the single-step power sets
-// (T^(j 512^l), three products at most), higher bits through T^(2^k).
-template <int NW>
-__device__ void warp_advance(const u32 *psets0, const u32 *tables, u32 (&v)[NW], u64 e, int lane)
-{
-    constexpr int n = NW * 32;
-    const size_t set_words = (size_t)PSET_SIZE * n * NW;
-    for (int l = 0; l < PSET_LEVELS; ++l) {
-        const u32 j = (u32)(e >> (PSET_BITS * l)) & (PSET_SIZE - 1);
-        if (j) warp_matvec<NW>(psets0 + l * set_words + (size_t)j * n * NW, v, lane);
-    }
-    u64 hi = e >> (PSET_BITS * PSET_LEVELS);
-    while (hi) {
-        const int k = __ffsll((long long)hi) - 1;
-        hi &= hi - 1;
-        warp_matvec<NW>(tables + (size_t)((PSET_BITS * PSET_LEVELS + k) % n) * n * NW, v, lane);
-    }
-}
-
 // One client's admitted requests in order, by one warp: each request gets the
 // current state in its 32-byte destination (req.slot indexes `rslots`: a
 // round's segment states, at the request's first segment, or a plain slot),
@@ -132,7 +76,7 @@ __device__ void admit_chain(const u32 *psets0, const u32 *tables, u32 *cstate, c
 #pragma unroll
             for (int w = 0; w < 8; ++w) d[w] = w < NW ? v[w % NW] : 0u;
         }
-        warp_advance<NW>(psets0, tables, v, q.n, lane);
+        warp_advance<NW>(psets0, tables, 0, v, q.n, lane);
     }
     if (lane == 0) {
 #pragma unroll
