@@ -95,33 +95,46 @@ __global__ void k_batch_seed(BatchDev d, size_t nreq)
 
 // ---------------------------------------------------------------- segment starts
 
-// One level of the power-set scheme over many requests of one engine:
+// One level of the power-set scheme over many requests:
 // segstates[parent + j * stride] = P[j] segstates[parent] when inside the
-// request (below `limit`).  The CTA shares j, builds the Four-Russians tables
-// of P[j] in shared memory and handles two items per thread.  Items come
-// longest first, so a CTA whose first item has no child j has nothing to do
-// and leaves before building its tables.
+// request (below `limit`).  One launch serves every engine of the level: the
+// x-range of each engine's CTAs is a field of LevelArgs.  A CTA shares j,
+// builds the Four-Russians tables of P[j] in shared memory and handles two
+// items per thread.  Items come longest first, so a CTA whose first item has
+// no child j has nothing to do and leaves before building its tables.
 constexpr int BLEVEL_ITEMS_PER_THREAD = 2;
+constexpr int BLEVEL_THREADS = 256;
+
+struct LevelEngine {
+    const u32 *P;             // the level's power set of this engine's distance
+    const BLevelItem *items;  // this engine's items, longest first
+    u64 nitems;
+    unsigned cta_first;       // first blockIdx.x of this engine
+    unsigned maxj;            // largest power-set index in use
+    int nw;                   // state words
+};
+struct LevelArgs {
+    LevelEngine e[NUM_PSET_ENGINES];
+    int n;
+    u64 stride;
+};
 
 template <int NW>
-__global__ void __launch_bounds__(256)
-    k_batch_level(const u32 *__restrict__ P, const BLevelItem *__restrict__ items, size_t nitems,
-                  u64 stride, u32 *segstates)
+__device__ __forceinline__ void batch_level_cta(const LevelEngine &E, unsigned x, int j, u64 stride, u32 *segstates,
+                                                u32 *T)
 {
     typedef Russians<NW> RT;
-    __shared__ __align__(16) u32 T[RT::WORDS];
-    const int j = blockIdx.y + 1;
     {
-        const BLevelItem lead = items[(size_t)blockIdx.x * BLEVEL_ITEMS_PER_THREAD * blockDim.x];
+        const BLevelItem lead = E.items[(size_t)x * BLEVEL_ITEMS_PER_THREAD * BLEVEL_THREADS];
         if (lead.parent + (u64)j * stride >= lead.limit) return;
     }
-    russians_build<NW>(P + (size_t)j * RT::n * NW, T);
+    russians_build<NW>(E.P + (size_t)j * RT::n * NW, T);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BLEVEL_ITEMS_PER_THREAD; ++k) {
-        const size_t idx = ((size_t)blockIdx.x * BLEVEL_ITEMS_PER_THREAD + k) * blockDim.x + threadIdx.x;
-        if (idx >= nitems) return;
-        const BLevelItem it = items[idx];
+        const size_t idx = ((size_t)x * BLEVEL_ITEMS_PER_THREAD + k) * BLEVEL_THREADS + threadIdx.x;
+        if (idx >= E.nitems) return;
+        const BLevelItem it = E.items[idx];
         const u64 child = it.parent + (u64)j * stride;
         if (child >= it.limit) continue;
         // 32-byte slots: whole 16-byte loads and stores (the unused words of a
@@ -148,6 +161,20 @@ __global__ void __launch_bounds__(256)
             cs[1] = make_uint4(0u, 0u, 0u, 0u);
         }
     }
+}
+
+__global__ void __launch_bounds__(BLEVEL_THREADS) k_batch_level(const LevelArgs a, u32 *segstates)
+{
+    __shared__ __align__(16) u32 T[Russians<8>::WORDS];
+    int k = 0;
+    while (k + 1 < a.n && blockIdx.x >= a.e[k + 1].cta_first) ++k;
+    const LevelEngine &E = a.e[k];
+    const int j = blockIdx.y + 1;
+    if ((unsigned)j > E.maxj) return;
+    const unsigned x = blockIdx.x - E.cta_first;
+    if (E.nw == 8) batch_level_cta<8>(E, x, j, a.stride, segstates, T);
+    else if (E.nw == 4) batch_level_cta<4>(E, x, j, a.stride, segstates, T);
+    else batch_level_cta<2>(E, x, j, a.stride, segstates, T);
 }
 
 // ---------------------------------------------------------------- persistent fill
@@ -617,21 +644,30 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
         count_launch();
         err = cudaGetLastError();
     }
-    for (size_t i = 0; i < p.levels.size() && err == cudaSuccess; ++i) {
-        const LevelLaunch &L = p.levels[i];
-        const int di = pset_index(L.engine, BSEG_LOG2);
-        const int n = engine_bits(L.engine);
-        const size_t set_words = (size_t)PSET_SIZE * n * (n / 32);
-        const uint32_t *P = pset_sets(ctx, L.engine, di) + (size_t)L.level * set_words;
-        const size_t per_cta = (size_t)256 * BLEVEL_ITEMS_PER_THREAD;
-        const dim3 grid((unsigned)((L.count + per_cta - 1) / per_cta), L.maxj);
-        const u64 stride = 1ull << (PSET_BITS * L.level);
-        if (n == 256)
-            k_batch_level<8><<<grid, 256, 0, st>>>(P, items + L.first, L.count, stride, dp.segstates);
-        else if (n == 128)
-            k_batch_level<4><<<grid, 256, 0, st>>>(P, items + L.first, L.count, stride, dp.segstates);
-        else
-            k_batch_level<2><<<grid, 256, 0, st>>>(P, items + L.first, L.count, stride, dp.segstates);
+    // one launch per level, every engine of the level in it (p.levels is
+    // ordered by level, highest first)
+    for (size_t i = 0; i < p.levels.size() && err == cudaSuccess;) {
+        LevelArgs a;
+        a.n = 0;
+        a.stride = 1ull << (PSET_BITS * p.levels[i].level);
+        unsigned ctas = 0, maxj = 0;
+        const size_t per_cta = (size_t)BLEVEL_THREADS * BLEVEL_ITEMS_PER_THREAD;
+        const int level = p.levels[i].level;
+        for (; i < p.levels.size() && p.levels[i].level == level; ++i) {
+            const LevelLaunch &L = p.levels[i];
+            const int n = engine_bits(L.engine);
+            const size_t set_words = (size_t)PSET_SIZE * n * (n / 32);
+            LevelEngine &E = a.e[a.n++];
+            E.P = pset_sets(ctx, L.engine, pset_index(L.engine, BSEG_LOG2)) + (size_t)L.level * set_words;
+            E.items = items + L.first;
+            E.nitems = L.count;
+            E.cta_first = ctas;
+            E.maxj = L.maxj;
+            E.nw = n / 32;
+            ctas += (unsigned)((L.count + per_cta - 1) / per_cta);
+            maxj = std::max(maxj, L.maxj);
+        }
+        k_batch_level<<<dim3(ctas, maxj), BLEVEL_THREADS, 0, st>>>(a, dp.segstates);
         count_launch();
         err = cudaGetLastError();
     }
