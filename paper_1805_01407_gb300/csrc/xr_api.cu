@@ -629,8 +629,9 @@ extern "C" int xr_fill_seq_noalloc(xr_ctx *ctx, int variant, void *d_state, size
     const size_t seg = (size_t)1 << SEQ_LOG2_NOALLOC;
     const size_t full = n / seg, tail = n % seg, P = full + (tail ? 1 : 0);
     const size_t sb = (size_t)xr_state_bytes(variant);
-    // Every slot read below is written first in this call (the base copy and
-    // the doubling tree fill slots 0 .. P-1), so nothing has to start at zero.
+    // Every slot read below is written first in this call (make_streams fills
+    // slots 0 .. P-1: the base copy, then the stream starts), so nothing has
+    // to start at zero.
     cudaError_t err = make_streams(ctx, variant, SEQ_LOG2_NOALLOC, d_state, 0, P, scratch, st);
     if (err == cudaSuccess && full)
         err = launch_fill(variant, dtype, XR_STREAM_MAJOR, scratch, full, seg, seg, d_out, 1,
