@@ -54,7 +54,7 @@ def parse_args():
     p.add_argument("--no-jumpstart", action="store_true")
     p.add_argument("--serve-requests", type=int, default=20000)
     p.add_argument("--batched-steps", type=int, default=5)
-    p.add_argument("--profile", choices=["fill", "streams", "batch", "lc", "lc-bulk"], default=None,
+    p.add_argument("--profile", choices=["fill", "streams", "fused", "batch", "lc", "lc-bulk"], default=None,
                    help="run a small case for an ncu capture instead of the benchmark")
     p.add_argument("--profile-variant", default="xoshiro256**")
     p.add_argument("--profile-dtype", default=None)
@@ -651,8 +651,9 @@ def run_jumpstart(xr, ctx, args):
     """Jump-start at scale: 2^24 xoshiro256++ streams J^i(s0) and L^i(s0) from
     SplitMix64(42), then 64 u64 outputs each; stream starts and fill timed
     with events on their stream (median of 3), then both pipelined over 16
-    chunks on two streams.  A stream start is one 256 x 256 F2
-    matrix-vector product (three power-set levels)."""
+    chunks on two streams, then fused in one kernel (xr_fill_streams).  A
+    stream start is one 256 x 256 F2 matrix-vector product (three power-set
+    levels)."""
     import torch
     c = W.CONFIG_JUMPSTART
     v, S, m = c["variant"], c["S"], c["m"]
@@ -700,12 +701,18 @@ def run_jumpstart(xr, ctx, args):
         check = int(out.view(torch.int64).sum())
         ms_pipe = timed(lambda: pipelined(kind))
         same = int(out.view(torch.int64).sum()) == check
+        out.zero_()
+        ms_fused = timed(lambda: ctx.fill_streams(v, kind, base, 0, S, m, "u64", out))
+        same_fused = int(out.view(torch.int64).sum()) == check
         res[kind] = {"streams_ms": ms_streams, "streams_per_s": S / (ms_streams / 1e3),
                      "fill_ms": ms_fill, "fill_gbs": S * m * 8 / (ms_fill / 1e3) / 1e9,
                      "fill_frac_of_measured_peak": S * m * 8 / (ms_fill / 1e3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
                      "total_gbs": S * m * 8 / ((ms_streams + ms_fill) / 1e3) / 1e9,
                      "pipelined_ms": ms_pipe, "pipelined_gbs": S * m * 8 / (ms_pipe / 1e3) / 1e9,
-                     "pipelined_chunks": chunks, "pipelined_same_output": same}
+                     "pipelined_chunks": chunks, "pipelined_same_output": same,
+                     "fused_ms": ms_fused, "fused_gbs": S * m * 8 / (ms_fused / 1e3) / 1e9,
+                     "fused_frac_of_measured_peak": S * m * 8 / (ms_fused / 1e3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
+                     "fused_same_output": same_fused}
     del out, states
     torch.cuda.synchronize()
     assert ctx.status() == 0
@@ -811,7 +818,8 @@ def d2h_link_gbs(h_out):
 def run_profile(args):
     """A small case for ncu: one warm-up launch, then --profile-launches launches
     of the profiled kernel (fill: 2^16 streams x 2^10 outputs = 512 MiB of u64,
-    larger than L2; streams: jump-start of --profile-streams streams)."""
+    larger than L2; streams: jump-start of --profile-streams streams; fused:
+    xr_fill_streams of --profile-streams streams x 64 outputs)."""
     import torch
     import paper_1805_01407_gb300 as xr
     from paper_1805_01407_gb300 import build as libbuild
@@ -823,9 +831,19 @@ def run_profile(args):
     v = args.profile_variant
     d = args.profile_dtype or W.native_dtype(v)
     S, m = args.profile_streams, W.CONFIG_BULK["m"]
+    if args.profile == "fused":  # the jump-start shape: 64 outputs per stream
+        m = W.CONFIG_JUMPSTART["m"]
     with xr.Context(0) as ctx:
         base = ctx.empty_states(v, 1)
         ctx.seed(v, W.CONFIG_BULK["seed"], base)
+        if args.profile == "fused":
+            out = ctx.empty_output(S * m, d)
+            for _ in range(1 + args.profile_launches):
+                ctx.fill_streams(v, "jump", base, 0, S, m, d, out)
+            torch.cuda.synchronize()
+            assert ctx.status() == 0
+            print("profile case done: %s %s S=%d m=%d" % (args.profile, v, S, m))
+            return 0
         states = ctx.empty_states(v, S)
         ctx.make_streams(v, "jump", base, 0, S, states)
         out = ctx.empty_output(S * m, d) if args.profile == "fill" else None

@@ -183,6 +183,28 @@ int xr_make_streams(xr_ctx *ctx, int variant, int kind, const void *d_base, uint
 int xr_fill(xr_ctx *ctx, int variant, void *d_states, size_t S, size_t m, int dtype, int layout,
             void *d_out, int write_back, void *stream);
 
+/* xr_fill_streams: xr_make_streams followed by xr_fill, without a state table
+ * in global memory.  Stream i = J^(first + i)(d_base) for i < S (the jump or
+ * long jump, Sec. 5; jumps as products with T^J, Sec. 6) emits m outputs of
+ * next(), converted to dtype, at d_out[i * m .. i * m + m - 1] (stream-major).
+ * One kernel computes each stream's start state in the thread that then
+ * generates it: stream 512 p + j from P_0[j] = (T^J)^j applied to stream
+ * 512 p.  The states are not written back (use xr_make_streams and xr_fill
+ * with write_back to continue sequences).
+ *   - d_base: one state (device), read only; d_out: S * m elements of dtype
+ *     (device, aligned to the element size; 16-byte aligned with m * element
+ *     size a multiple of 16 bytes for the fused kernel).
+ *   - Uses the context scratch (grown with cudaMalloc when too small: 32
+ *     bytes per 512 streams on the fused path); not safe to call concurrently
+ *     with xr_fill_seq or another xr_fill_streams on the same context.
+ *   - Up to 2^27 streams per call (and any S mod 512 tail) take the fused
+ *     kernel; the 512- and 1024-bit generators, larger S and shapes the tile
+ *     store cannot describe make a state table in the scratch instead
+ *     (S x state bytes), with the same results.
+ *   - XR_EINVAL for bad arguments; S = 0 or m = 0 is a valid no-op. */
+int xr_fill_streams(xr_ctx *ctx, int variant, int kind, const void *d_base, uint64_t first, size_t S, size_t m,
+                    int dtype, void *d_out, void *stream);
+
 /* xr_fill_seq: the first n outputs of one sequence starting at d_state, into
  * d_out (n elements of dtype); d_state is then advanced by n steps.  The
  * sequence is split into segments of 2^10 outputs whose start states are

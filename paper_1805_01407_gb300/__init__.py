@@ -99,6 +99,7 @@ def lib():
             "xr_make_streams": [vp, i, i, vp, u64, sz, vp, vp],
             "xr_fill": [vp, i, vp, sz, sz, i, i, vp, i, vp],
             "xr_fill_seq": [vp, i, vp, sz, i, vp, vp],
+            "xr_fill_streams": [vp, i, i, vp, u64, sz, sz, i, vp, vp],
             "xr_fill_host": [vp, i, i, vp, u64, sz, sz, i, vp, vp],
             "xr_status": [vp, i],
             "xr_jump_table": [vp, i, i, vp],
@@ -332,6 +333,12 @@ class Context:
         _check(lib().xr_fill(self._h, _v(variant), d_states.data_ptr(), S, m, DTYPES[dtype],
                              LAYOUTS[layout], d_out.data_ptr(), int(bool(write_back)),
                              _stream(stream)), "xr_fill")
+
+    def fill_streams(self, variant, kind, d_base, first, S, m, dtype, d_out, stream=None):
+        _need(d_base, state_bytes(variant), "d_base")
+        _need(d_out, S * m * dtype_bytes(dtype), "d_out")
+        _check(lib().xr_fill_streams(self._h, _v(variant), KINDS[kind], d_base.data_ptr(), first, S, m,
+                                     DTYPES[dtype], d_out.data_ptr(), _stream(stream)), "xr_fill_streams")
 
     def fill_seq(self, variant, d_state, n, dtype, d_out, stream=None):
         _need(d_state, state_bytes(variant), "d_state")

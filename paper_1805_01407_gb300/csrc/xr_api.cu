@@ -71,6 +71,30 @@ cudaError_t launch_fill(int variant, int dtype, int layout, void *states, size_t
     }
 }
 
+template <int V>
+cudaError_t launch_fill_streams_v(int dtype, const uint32_t *P0, const void *parents, size_t npar, size_t m,
+                                  void *out, int *status, cudaStream_t stream, EncodeTiledFn encode);
+#define XR_FS_EXTERN(V)                                                                                         \
+    extern template cudaError_t launch_fill_streams_v<V>(int, const uint32_t *, const void *, size_t, size_t, \
+                                                         void *, int *, cudaStream_t, EncodeTiledFn);
+XR_FS_EXTERN(0) XR_FS_EXTERN(1) XR_FS_EXTERN(2) XR_FS_EXTERN(3) XR_FS_EXTERN(4) XR_FS_EXTERN(5)
+XR_FS_EXTERN(6) XR_FS_EXTERN(7) XR_FS_EXTERN(8) XR_FS_EXTERN(9) XR_FS_EXTERN(10) XR_FS_EXTERN(11)
+#undef XR_FS_EXTERN
+
+// Fused stream starts + fill for the generators with power sets (0 .. 11).
+static cudaError_t launch_fill_streams(int variant, int dtype, const uint32_t *P0, const void *parents, size_t npar,
+                                       size_t m, void *out, int *status, cudaStream_t st, EncodeTiledFn encode)
+{
+#define XR_FS_CASE(V) \
+    case V: return launch_fill_streams_v<V>(dtype, P0, parents, npar, m, out, status, st, encode);
+    switch (variant) {
+        XR_FS_CASE(0) XR_FS_CASE(1) XR_FS_CASE(2) XR_FS_CASE(3) XR_FS_CASE(4) XR_FS_CASE(5)
+        XR_FS_CASE(6) XR_FS_CASE(7) XR_FS_CASE(8) XR_FS_CASE(9) XR_FS_CASE(10) XR_FS_CASE(11)
+    default: return cudaErrorNotSupported;
+    }
+#undef XR_FS_CASE
+}
+
 }  // namespace xr
 
 using namespace xr;
@@ -441,6 +465,79 @@ extern "C" int xr_make_streams(xr_ctx *ctx, int variant, int kind, const void *d
     }
     return status_of(make_streams(ctx, variant, xr_jump_log2(variant, kind), d_base, first, S,
                                   d_states_out, (cudaStream_t)stream));
+}
+
+// Streams J^(first + i)(base), i < S, m outputs each, without a state table
+// in global memory: the parents p (streams 512 p, i.e. J^(first + 512 p))
+// come from the two upper power-set levels of the jump distance, then one
+// fused launch starts and fills every stream 512 p + j from P_0[j] parent_p.
+// A tail of S mod 512 streams, engines without power sets, more than 2^27
+// streams and shapes the tile store cannot describe take make_streams + fill
+// over the context scratch.
+static cudaError_t ensure(void **p, size_t *have, size_t want);
+
+static cudaError_t fill_streams(xr_ctx *ctx, int variant, int d, const void *d_base, uint64_t first, size_t S,
+                                size_t m, int dtype, void *out, cudaStream_t st)
+{
+    const int e = engine_of(variant);
+    const int di = pset_index(e, d);
+    const size_t sb = (size_t)xr_state_bytes(variant), es = (size_t)xr_dtype_bytes(dtype);
+    const size_t npar = S / PSET_SIZE, tail = S % PSET_SIZE;
+    const size_t maxpar = (size_t)1 << (PSET_BITS * (PSET_LEVELS - 1));
+    // what the 3D tile store needs (the launcher checks the same)
+    const bool tiles_ok = ctx->encode && ((uintptr_t)out % 16) == 0 && ((m * es) % 16) == 0 && m < (1ull << 31) &&
+                          (size_t)PSET_SIZE * m * es < (1ull << 40);
+    cudaError_t err = cudaErrorNotSupported;
+    size_t done = 0;  // streams written by the fused path
+    if (di >= 0 && npar >= 1 && npar <= maxpar && tiles_ok) {
+        size_t cap = ctx->scratch_bytes;
+        err = ensure(&ctx->scratch, &cap, (npar + tail) * sb);
+        ctx->scratch_bytes = cap;
+        if (err != cudaSuccess) return err;
+        const uint32_t *sets = pset_sets(ctx, e, di);
+        const size_t set_words = (size_t)PSET_SIZE * engine_bits(e) * (engine_bits(e) / 32);
+        // parent 0 = J^first(base), then parents p = (T^(2^(d+9)))^p parent 0 from
+        // levels 1 and 2 of the jump power sets
+        if (first) err = launch_warp_jump(e, sets, ctx->tables[e], d, d_base, ctx->scratch, first, st);
+        else err = cudaMemcpyAsync(ctx->scratch, d_base, sb, cudaMemcpyDeviceToDevice, st);
+        if (err == cudaSuccess && npar > 1) err = launch_streams_psets(e, sets + set_words, ctx->scratch, npar, st);
+        if (err == cudaSuccess)
+            err = launch_fill_streams(variant, dtype, sets, ctx->scratch, npar, m, out, ctx->d_status, st,
+                                      ctx->encode);
+        if (err != cudaSuccess) return err;
+        done = npar * PSET_SIZE;
+    }
+    const size_t rest = S - done;
+    if (rest == 0) return cudaSuccess;
+    // the remaining streams through a state table
+    const size_t off = done ? npar * sb : 0;
+    size_t cap = ctx->scratch_bytes;
+    err = ensure(&ctx->scratch, &cap, off + rest * sb);
+    ctx->scratch_bytes = cap;
+    if (err != cudaSuccess) return err;
+    void *states = (char *)ctx->scratch + off;
+    err = make_streams(ctx, variant, d, d_base, first + done, rest, states, st);
+    if (err == cudaSuccess)
+        err = launch_fill(variant, dtype, XR_STREAM_MAJOR, states, rest, m, m, (char *)out + done * m * es, 0,
+                          ctx->d_status, st, ctx->encode);
+    return err;
+}
+
+extern "C" int xr_fill_streams(xr_ctx *ctx, int variant, int kind, const void *d_base, uint64_t first, size_t S,
+                               size_t m, int dtype, void *d_out, void *stream)
+{
+    if (!ctx || !variant_ok(variant) || !dtype_ok(variant, dtype)) return XR_EINVAL;
+    if (kind != XR_JUMP && kind != XR_LONG_JUMP) return XR_EINVAL;
+    DeviceScope dscope(ctx->device);
+    if (S == 0 || m == 0) return XR_OK;
+    const size_t es = (size_t)xr_dtype_bytes(dtype);
+    if (!states_ok(d_base) || !d_out || ((uintptr_t)d_out % es) || m > (SIZE_MAX / es) / S) return XR_EINVAL;
+    {
+        const int erc = ensure_engine(ctx, engine_of(variant));
+        if (erc != XR_OK) return erc;
+    }
+    return status_of(fill_streams(ctx, variant, xr_jump_log2(variant, kind), d_base, first, S, m, dtype, d_out,
+                                  (cudaStream_t)stream));
 }
 
 // ---------------------------------------------------------------- generation

@@ -8,4 +8,7 @@ namespace xr {
 XR_FILL_INST(9) XR_FILL_INST(10) XR_FILL_INST(11) XR_FILL_INST(12) XR_FILL_INST(13)
 XR_FILL_INST(14) XR_FILL_INST(15) XR_FILL_INST(16) XR_FILL_INST(17)
 #undef XR_FILL_INST
+template cudaError_t launch_fill_streams_v<9>(int, const uint32_t *, const void *, size_t, size_t, void *, int *, cudaStream_t, EncodeTiledFn);
+template cudaError_t launch_fill_streams_v<10>(int, const uint32_t *, const void *, size_t, size_t, void *, int *, cudaStream_t, EncodeTiledFn);
+template cudaError_t launch_fill_streams_v<11>(int, const uint32_t *, const void *, size_t, size_t, void *, int *, cudaStream_t, EncodeTiledFn);
 }  // namespace xr

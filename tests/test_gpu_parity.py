@@ -373,6 +373,62 @@ def test_jumpstart_configuration_sampled(ctx, xr, kind):
         assert_bits_equal(rows[r], raw, "stream %d" % i)
 
 
+# (S, first, m): one stream; below one parent; one parent; parent + tail; a
+# high first with a tail; a row length the tile store cannot take (state
+# table path); two CTA rows of parents (8 warps x 32 parents each) + a tail
+FILL_STREAMS_CASES = [(1, 0, 16), (511, 3, 8), (512, 0, 64), (513, 7, 64), (3 * 512 + 100, 2**40 + 1, 24),
+                      (1024, 5, 5), (2 * 256 * 512 + 3, 11, 4)]
+
+
+@pytest.mark.parametrize("name", ["xoshiro256++", "xoroshiro128**", "xoroshiro128++", "xoshiro128**",
+                                  "xoroshiro64*", "xoshiro512++"])
+@pytest.mark.parametrize("kind", ["jump", "long"])
+def test_fill_streams(ctx, xr, name, kind):
+    """xr_fill_streams (stream starts fused with the fill) against the
+    oracle's J^(first + i)(base) streams and their outputs, every dtype, with
+    canaries around the output."""
+    import torch
+    base = O.seed(name, 7)
+    d_base = states_to_device(name, base[None, :])
+    for S, first, m in FILL_STREAMS_CASES:
+        raw = O.bulk_fill(name, kind, base, S, m, first=first).reshape(-1)
+        for dtype in (xr.native_dtype(name), "f64", "f32"):
+            buf, view, start, nb = guarded_output(xr, S * m, dtype)
+            ctx.fill_streams(name, kind, d_base, first, S, m, dtype, as_dtype(view, dtype))
+            torch.cuda.synchronize()
+            check_canaries(buf, start, nb)
+            got = out_to_numpy(as_dtype(view, dtype), dtype)
+            assert_bits_equal(got, expected(name, raw, dtype),
+                              "%s %s %s S=%d first=%d m=%d" % (name, kind, dtype, S, first, m))
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("kind", ["jump", "long"])
+def test_jumpstart_configuration_fused_sampled(ctx, xr, kind):
+    """The jump-start configuration (2^24 xoshiro256++ streams x 64 u64
+    outputs) through xr_fill_streams: 4096 sampled streams against the
+    oracle's jump power and outputs, and the first 1024 rows in full."""
+    import torch
+    c = W.CONFIG_JUMPSTART
+    name, S, m = c["variant"], c["S"], c["m"]
+    base = O.seed(name, c["seed"])
+    d = O.jump_log2(name, kind)
+    d_base = ctx.empty_states(name, 1)
+    ctx.seed(name, c["seed"], d_base)
+    out = ctx.empty_output(S * m, "u64")
+    ctx.fill_streams(name, kind, d_base, 0, S, m, "u64", out)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    head = out_to_numpy(out[:1024 * m], "u64")
+    assert_bits_equal(head, O.bulk_fill(name, kind, base, 1024, m).reshape(-1), "first 1024 streams")
+    idx = W.sample_indices(S, c["samples"], c["sample_seed"])
+    rows = out_to_numpy(out.view(S, m)[torch.as_tensor(idx, device="cuda")].contiguous(), "u64")
+    rows = rows.reshape(len(idx), m)
+    for r, i in enumerate(idx):
+        raw, _ = O.generate(name, O.jump_pow(name, d, int(i), base), m)
+        assert_bits_equal(rows[r], raw, "stream %d" % i)
+
+
 def test_fill_host_chunks(ctx, xr):
     """End-to-end call into host memory, large enough for three staging chunks."""
     import torch
