@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "xr_device.cuh"
+#include "xr_f2.cuh"
 #include "xr_internal.h"
 
 namespace xr {

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "xr_device.cuh"
+#include "xr_f2.cuh"
 #include "xr_fill_impl.cuh"
 #include "xr_internal.h"
 #include "xr_batch_plan.h"

@@ -1,6 +1,6 @@
 // xr_fill_more.cu -- fill kernels of generators 9 .. 17 (xoroshiro128*, the
 // 32-bit xoroshiro64 pair, xoshiro512 and xoroshiro1024; see xr_fill_impl.cuh).
-#include "xr_fill_impl.cuh"
+#include "xr_fill_streams.cuh"
 
 namespace xr {
 #define XR_FILL_INST(V) \

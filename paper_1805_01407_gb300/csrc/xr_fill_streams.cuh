@@ -1,0 +1,157 @@
+// xr_fill_streams.cuh -- stream starts fused with the fill (xr_fill_streams):
+// the fill kernels' tile staging (xr_fill_impl.cuh) fed by start states that
+// each thread computes from the power sets (xr_f2.cuh).
+#pragma once
+
+#include "xr_f2.cuh"
+#include "xr_fill_impl.cuh"
+
+namespace xr {
+
+// ---------------------------------------------------------------- stream starts fused with the fill
+//
+// Streams i = 512 p + j of a range whose parents (streams 512 p) are given:
+// stream i starts at P_0[j] parent_p, with P_0[j] = T^(2^d j) the level-0
+// power set of the jump distance 2^d (Sec. 5, 6).  A CTA takes one j and
+// FS_WARPS x FS_GROUPS x 32 parents: it builds the Four-Russians tables of
+// P_0[j] once; a warp then takes its groups of 32 parents in turn, every lane
+// taking its start state from one table product and generating its m outputs
+// like k_fill_tma, so the tile stores of one group drain while the next
+// group's products run.  Lanes of a warp are rows 512 apart, so the tile store
+// goes through a 3D tensor map (columns, j, p).  The start states never reach
+// global memory; each lane keeps its own in a shared-memory slot for the rare
+// exact redo of a double row.
+constexpr int FS_WARPS = 8;
+constexpr int FS_NBUF = 2;
+constexpr int FS_GROUPS = 4;  // groups of 32 parents per warp, one after another
+constexpr int FS_CHILDREN = PSET_SIZE;  // streams per parent
+
+template <int V>
+struct FuseCfg {
+    typedef typename Gen<V>::E E;
+    static constexpr int NW = (int)sizeof(E::s) / 4;
+    static constexpr int TABLE_BYTES = Russians<NW>::WORDS * 4;
+    static constexpr int SMEM = FS_WARPS * FS_NBUF * TILE_BYTES + TABLE_BYTES + FS_WARPS * 32 * 32 + 1024;
+};
+
+template <int V, int DT>
+__global__ void __launch_bounds__(FS_WARPS * 32)
+    k_fill_streams(const __grid_constant__ CUtensorMap map, const u32 *__restrict__ P0, const u32 *parents,
+                   size_t npar, size_t m, int *status)
+{
+    typedef Gen<V> G;
+    typedef typename G::E E;
+    constexpr int NW = FuseCfg<V>::NW;
+    typedef Russians<NW> RT;
+    constexpr int COLS = 128 / (int)sizeof(typename OutElem<DT>::type);
+    extern __shared__ unsigned char dyn_smem[];
+    const u32 pad = ((smem_addr(dyn_smem) + 1023u) & ~1023u) - smem_addr(dyn_smem);
+    const u32 base = smem_addr(dyn_smem) + pad;                     // tiles, 1024-byte aligned
+    u32 *T = reinterpret_cast<u32 *>(dyn_smem + pad + FS_WARPS * FS_NBUF * TILE_BYTES);
+    unsigned char *slots = reinterpret_cast<unsigned char *>(T + RT::WORDS);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x;
+    russians_build<NW>(P0 + (size_t)j * RT::n * NW, T);
+    __syncthreads();
+    const u32 tiles = base + (u32)(warp * FS_NBUF * TILE_BYTES);
+    unsigned char *slot = slots + (warp * 32 + lane) * 32;
+    int it = 0;
+    for (int g = 0; g < FS_GROUPS; ++g) {
+        const size_t p0 = (((size_t)blockIdx.y * FS_GROUPS + g) * FS_WARPS + warp) * 32;
+        if (p0 >= npar) break;
+        const bool live = p0 + lane < npar;
+        u32 v[NW], r[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) v[w] = 0u;
+        if (live) {
+            const u32 *ps = parents + (p0 + lane) * NW;  // 16-byte loads (8-byte for 64-bit states)
+            if constexpr (NW >= 4) {
+#pragma unroll
+                for (int q = 0; q < NW / 4; ++q) {
+                    const uint4 a = reinterpret_cast<const uint4 *>(ps)[q];
+                    v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+                }
+            } else {
+                const uint2 a = reinterpret_cast<const uint2 *>(ps)[0];
+                v[0] = a.x; v[1] = a.y;
+            }
+        }
+        russians_matvec<NW>(T, v, r);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) reinterpret_cast<u32 *>(slot)[w] = r[w];
+        E e;
+        load_state(e, slot);
+        if (live && state_is_zero(e)) atomicCAS(status, 0, XR_EZERO_STATE);
+        for (size_t j0 = 0; j0 < m; j0 += COLS, ++it) {
+            const u32 tile = tiles + (u32)((it % FS_NBUF) * TILE_BYTES);
+            if (it >= FS_NBUF) {
+                if (lane == 0) bulk_wait_read<FS_NBUF - 1>();
+                __syncwarp();
+            }
+            fill_tile_row<G, DT>(e, tile, lane, m - j0, live, slot, j0);
+            fence_proxy_async_shared();
+            __syncwarp();
+            if (lane == 0) {
+                tma_store_3d(&map, tile, (int)j0, j, (int)p0);
+                bulk_commit();
+            }
+        }
+    }
+    if (lane == 0) bulk_wait_read<0>();
+}
+
+// npar parents (contiguous states) -> npar * 512 streams x m outputs in d_out
+// (stream-major).  cudaErrorNotSupported when the shape does not suit the
+// tile store (the caller then takes another path).
+template <int V, int DT>
+cudaError_t launch_fill_streams_vd(const u32 *P0, const void *parents, size_t npar, size_t m, void *out,
+                                   int *status, cudaStream_t stream, EncodeTiledFn encode)
+{
+    constexpr int ES = (int)sizeof(typename OutElem<DT>::type);
+    constexpr int COLS = 128 / ES;
+    typedef FuseCfg<V> FC;
+    if (!encode || ((uintptr_t)out % 16) || ((m * ES) % 16) || m == 0 || m >= (1ull << 31) ||
+        npar >= (1ull << 31) || (size_t)FS_CHILDREN * m * ES >= (1ull << 40))
+        return cudaErrorNotSupported;
+    const size_t gy = (npar + FS_GROUPS * FS_WARPS * 32 - 1) / (FS_GROUPS * FS_WARPS * 32);
+    if (gy > 65535) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)m, (cuuint64_t)FS_CHILDREN, (cuuint64_t)npar};
+    const cuuint64_t strides[2] = {(cuuint64_t)(m * ES), (cuuint64_t)((size_t)FS_CHILDREN * m * ES)};
+    const cuuint32_t box[3] = {(cuuint32_t)COLS, 1u, 32u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (encode(&map, ES == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, out, dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorNotSupported;
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t ea = set_smem_once(attr, k_fill_streams<V, DT>, FC::SMEM);
+    if (ea != cudaSuccess) return ea;
+    k_fill_streams<V, DT><<<dim3(FS_CHILDREN, (unsigned)gy), FS_WARPS * 32, FC::SMEM, stream>>>(
+        map, P0, (const u32 *)parents, npar, m, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int V>
+cudaError_t launch_fill_streams_v(int dtype, const uint32_t *P0, const void *parents, size_t npar, size_t m,
+                                  void *out, int *status, cudaStream_t stream, EncodeTiledFn encode)
+{
+    constexpr bool w64 = sizeof(typename Gen<V>::word) == 8;
+    switch (dtype) {
+    case DT_U64:
+        if constexpr (w64) return launch_fill_streams_vd<V, DT_U64>(P0, parents, npar, m, out, status, stream, encode);
+        return cudaErrorInvalidValue;
+    case DT_U32:
+        if constexpr (!w64) return launch_fill_streams_vd<V, DT_U32>(P0, parents, npar, m, out, status, stream, encode);
+        return cudaErrorInvalidValue;
+    case DT_F64:
+        return launch_fill_streams_vd<V, DT_F64>(P0, parents, npar, m, out, status, stream, encode);
+    case DT_F32:
+        return launch_fill_streams_vd<V, DT_F32>(P0, parents, npar, m, out, status, stream, encode);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace xr

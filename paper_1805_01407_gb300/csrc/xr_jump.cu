@@ -10,6 +10,7 @@
 #include <algorithm>
 
 #include "xr_device.cuh"
+#include "xr_f2.cuh"
 #include "xr_internal.h"
 
 namespace xr {

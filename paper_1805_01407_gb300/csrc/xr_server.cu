@@ -24,6 +24,7 @@
 
 #include "xr_batch_plan.h"
 #include "xr_device.cuh"
+#include "xr_f2.cuh"
 #include "xr_internal.h"
 
 namespace xr {
