@@ -183,24 +183,30 @@ int xr_make_streams(xr_ctx *ctx, int variant, int kind, const void *d_base, uint
 int xr_fill(xr_ctx *ctx, int variant, void *d_states, size_t S, size_t m, int dtype, int layout,
             void *d_out, int write_back, void *stream);
 
-/* xr_fill_streams: xr_make_streams followed by xr_fill, without a state table
- * in global memory.  Stream i = J^(first + i)(d_base) for i < S (the jump or
- * long jump, Sec. 5; jumps as products with T^J, Sec. 6) emits m outputs of
- * next(), converted to dtype, at d_out[i * m .. i * m + m - 1] (stream-major).
- * One kernel computes each stream's start state in the thread that then
- * generates it: stream 512 p + j from P_0[j] = (T^J)^j applied to stream
- * 512 p.  The states are not written back (use xr_make_streams and xr_fill
- * with write_back to continue sequences).
+/* xr_fill_streams: xr_make_streams followed by xr_fill.  Stream
+ * i = J^(first + i)(d_base) for i < S (the jump or long jump, Sec. 5; jumps
+ * as products with T^J, Sec. 6) emits m outputs of next(), converted to
+ * dtype, at d_out[i * m .. i * m + m - 1] (stream-major).  For short rows
+ * one kernel computes each stream's start state in the thread that then
+ * generates it, with no state table in global memory: in chunks of 512 P
+ * streams (P a power of two, at least 32), stream p + P j of a chunk starts
+ * at (T^J)^(P j) applied to stream p.  The states are not written back (use
+ * xr_make_streams and xr_fill with write_back to continue sequences).
  *   - d_base: one state (device), read only; d_out: S * m elements of dtype
- *     (device, aligned to the element size; 16-byte aligned with m * element
- *     size a multiple of 16 bytes for the fused kernel).
- *   - Uses the context scratch (grown with cudaMalloc when too small: 32
- *     bytes per 512 streams on the fused path); not safe to call concurrently
- *     with xr_fill_seq or another xr_fill_streams on the same context.
- *   - Up to 2^27 streams per call (and any S mod 512 tail) take the fused
- *     kernel; the 512- and 1024-bit generators, larger S and shapes the tile
- *     store cannot describe make a state table in the scratch instead
- *     (S x state bytes), with the same results.
+ *     (device, aligned to the element size).
+ *   - The fused kernel takes rows of at most 512 bytes (m * element size a
+ *     multiple of 16, d_out 16-byte aligned), engines of at most 256 bits,
+ *     and chunks while at least 512 x 32 streams are left.  Everything else
+ *     (longer rows, where it measured slower, the rest below 512 x 32 streams,
+ *     the 512- and 1024-bit generators) goes through a state table, with the
+ *     same results.
+ *   - The first call that needs the power set of a new distance 2^J P builds
+ *     and keeps it in the context (3 x 512 matrices: 12 MiB for 256-bit
+ *     states, with cudaMalloc) and waits for the device once.
+ *   - Uses the context scratch (grown with cudaMalloc when too small: P
+ *     states for a chunk, S states on the state-table path); not safe to call
+ *     concurrently with xr_fill_seq or another xr_fill_streams on the same
+ *     context.
  *   - XR_EINVAL for bad arguments; S = 0 or m = 0 is a valid no-op. */
 int xr_fill_streams(xr_ctx *ctx, int variant, int kind, const void *d_base, uint64_t first, size_t S, size_t m,
                     int dtype, void *d_out, void *stream);

@@ -241,6 +241,26 @@ const uint32_t *pset_sets(const xr_ctx *ctx, int engine, int di)
     const size_t set_words = (size_t)PSET_SIZE * n * (n / 32);
     return ctx->psets[engine] + (size_t)di * PSET_LEVELS * set_words;
 }
+
+const uint32_t *dist_sets(xr_ctx *ctx, int engine, int d)
+{
+    if (engine >= NUM_PSET_ENGINES || d < 0 || d >= engine_bits(engine) || !ctx->tables[engine]) return nullptr;
+    uint32_t *p = __atomic_load_n(&ctx->dist_sets[engine][d], __ATOMIC_ACQUIRE);
+    if (p) return p;
+    std::lock_guard<std::mutex> lk(*(std::mutex *)ctx->lazy_mutex);
+    p = ctx->dist_sets[engine][d];
+    if (p) return p;
+    const size_t n = (size_t)engine_bits(engine);
+    cudaError_t e = cudaMalloc((void **)&p, (size_t)PSET_LEVELS * PSET_SIZE * n * (n / 32) * 4);
+    if (e == cudaSuccess) e = launch_build_power_sets(engine, ctx->tables[engine], &d, 1, p, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return nullptr;
+    }
+    __atomic_store_n(&ctx->dist_sets[engine][d], p, __ATOMIC_RELEASE);
+    return p;
+}
 }  // namespace xr
 
 extern "C" int xr_ctx_destroy(xr_ctx *ctx)
@@ -251,6 +271,7 @@ extern "C" int xr_ctx_destroy(xr_ctx *ctx)
     for (int e = 0; e < NUM_ENGINES; ++e) {
         cudaFree(ctx->tables[e]);
         cudaFree(ctx->psets[e]);
+        for (int d = 0; d < 256; ++d) cudaFree(ctx->dist_sets[e][d]);
     }
     cudaFree(ctx->d_status);
     cudaFree(ctx->scratch);
@@ -468,57 +489,61 @@ extern "C" int xr_make_streams(xr_ctx *ctx, int variant, int kind, const void *d
 }
 
 // Streams J^(first + i)(base), i < S, m outputs each, without a state table
-// in global memory: the parents p (streams 512 p, i.e. J^(first + 512 p))
-// come from the two upper power-set levels of the jump distance, then one
-// fused launch starts and fills every stream 512 p + j from P_0[j] parent_p.
-// A tail of S mod 512 streams, engines without power sets, more than 2^27
-// streams and shapes the tile store cannot describe take make_streams + fill
-// over the context scratch.
+// in global memory.  In chunks of 512 P streams, P the largest power of two
+// (at least 32) that fits: the P parents are streams first + done + p
+// (xr_make_streams over the scratch), and stream p + P j of the chunk starts
+// at P_0[j] parent_p with P_0 the level-0 power set of the distance
+// 2^(d + log2 P) (built once per distance and cached).  The lanes of a warp
+// are then 32 consecutive streams sharing one matrix.  Rows over 512 bytes,
+// fewer than 512 x 32 streams left, engines without power sets and shapes
+// the tile store cannot describe go through a state table in the scratch.
 static cudaError_t ensure(void **p, size_t *have, size_t want);
 
 static cudaError_t fill_streams(xr_ctx *ctx, int variant, int d, const void *d_base, uint64_t first, size_t S,
                                 size_t m, int dtype, void *out, cudaStream_t st)
 {
     const int e = engine_of(variant);
-    const int di = pset_index(e, d);
+    const int n = engine_bits(e);
     const size_t sb = (size_t)xr_state_bytes(variant), es = (size_t)xr_dtype_bytes(dtype);
-    const size_t npar = S / PSET_SIZE, tail = S % PSET_SIZE;
-    const size_t maxpar = (size_t)1 << (PSET_BITS * (PSET_LEVELS - 1));
-    // what the 3D tile store needs (the launcher checks the same)
-    const bool tiles_ok = ctx->encode && ((uintptr_t)out % 16) == 0 && ((m * es) % 16) == 0 && m < (1ull << 31) &&
-                          (size_t)PSET_SIZE * m * es < (1ull << 40);
-    cudaError_t err = cudaErrorNotSupported;
-    size_t done = 0;  // streams written by the fused path
-    if (di >= 0 && npar >= 1 && npar <= maxpar && tiles_ok) {
-        size_t cap = ctx->scratch_bytes;
-        err = ensure(&ctx->scratch, &cap, (npar + tail) * sb);
-        ctx->scratch_bytes = cap;
-        if (err != cudaSuccess) return err;
-        const uint32_t *sets = pset_sets(ctx, e, di);
-        const size_t set_words = (size_t)PSET_SIZE * engine_bits(e) * (engine_bits(e) / 32);
-        // parent 0 = J^first(base), then parents p = (T^(2^(d+9)))^p parent 0 from
-        // levels 1 and 2 of the jump power sets
-        if (first) err = launch_warp_jump(e, sets, ctx->tables[e], d, d_base, ctx->scratch, first, st);
-        else err = cudaMemcpyAsync(ctx->scratch, d_base, sb, cudaMemcpyDeviceToDevice, st);
-        if (err == cudaSuccess && npar > 1) err = launch_streams_psets(e, sets + set_words, ctx->scratch, npar, st);
-        if (err == cudaSuccess)
-            err = launch_fill_streams(variant, dtype, sets, ctx->scratch, npar, m, out, ctx->d_status, st,
-                                      ctx->encode);
-        if (err != cudaSuccess) return err;
-        done = npar * PSET_SIZE;
+    // what the tile store needs (the launcher checks the same)
+    // short rows (at most 4 tiles of 128 bytes) that the tile store can take;
+    // the launcher checks the same
+    const bool tiles_ok = ctx->encode && ((uintptr_t)out % 16) == 0 && ((m * es) % 16) == 0 && m * es <= 512 &&
+                          S < (1ull << 31);
+    const size_t min_chunk = (size_t)PSET_SIZE * 32;
+    cudaError_t err = cudaSuccess;
+    size_t done = 0;  // streams written by the fused kernels
+    if (e < NUM_PSET_ENGINES && tiles_ok) {
+        while (S - done >= min_chunk) {
+            size_t P = 32;
+            int k = 5;
+            while (P * 2 * PSET_SIZE <= S - done) {
+                P *= 2;
+                ++k;
+            }
+            const uint32_t *Q = dist_sets(ctx, e, (d + k) % n);
+            if (!Q) return cudaErrorMemoryAllocation;
+            size_t cap = ctx->scratch_bytes;
+            err = ensure(&ctx->scratch, &cap, P * sb);
+            ctx->scratch_bytes = cap;
+            if (err == cudaSuccess) err = make_streams(ctx, variant, d, d_base, first + done, P, ctx->scratch, st);
+            if (err == cudaSuccess)
+                err = launch_fill_streams(variant, dtype, Q, ctx->scratch, P, m, (char *)out + done * m * es,
+                                          ctx->d_status, st, ctx->encode);
+            if (err != cudaSuccess) return err;
+            done += P * PSET_SIZE;
+        }
     }
     const size_t rest = S - done;
     if (rest == 0) return cudaSuccess;
     // the remaining streams through a state table
-    const size_t off = done ? npar * sb : 0;
     size_t cap = ctx->scratch_bytes;
-    err = ensure(&ctx->scratch, &cap, off + rest * sb);
+    err = ensure(&ctx->scratch, &cap, rest * sb);
     ctx->scratch_bytes = cap;
     if (err != cudaSuccess) return err;
-    void *states = (char *)ctx->scratch + off;
-    err = make_streams(ctx, variant, d, d_base, first + done, rest, states, st);
+    err = make_streams(ctx, variant, d, d_base, first + done, rest, ctx->scratch, st);
     if (err == cudaSuccess)
-        err = launch_fill(variant, dtype, XR_STREAM_MAJOR, states, rest, m, m, (char *)out + done * m * es, 0,
+        err = launch_fill(variant, dtype, XR_STREAM_MAJOR, ctx->scratch, rest, m, m, (char *)out + done * m * es, 0,
                           ctx->d_status, st, ctx->encode);
     return err;
 }

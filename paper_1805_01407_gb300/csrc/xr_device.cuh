@@ -372,17 +372,6 @@ __device__ __forceinline__ void fence_proxy_async_shared()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// 3D tile store shared -> global through the tensor map (cp.async.bulk.tensor).
-// Elements outside the tensor's extent are not written.
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, u32 src, int x, int y, int z)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
-            reinterpret_cast<uint64_t>(map)),
-        "r"(src), "r"(x), "r"(y), "r"(z)
-        : "memory");
-}
-
 // 2D tile store shared -> global through the tensor map (cp.async.bulk.tensor).
 // Elements outside the tensor's extent are not written.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, u32 src, int x, int y)

@@ -10,21 +10,24 @@ namespace xr {
 
 // ---------------------------------------------------------------- stream starts fused with the fill
 //
-// Streams i = 512 p + j of a range whose parents (streams 512 p) are given:
-// stream i starts at P_0[j] parent_p, with P_0[j] = T^(2^d j) the level-0
-// power set of the jump distance 2^d (Sec. 5, 6).  A CTA takes one j and
-// FS_WARPS x FS_GROUPS x 32 parents: it builds the Four-Russians tables of
-// P_0[j] once; a warp then takes its groups of 32 parents in turn, every lane
-// taking its start state from one table product and generating its m outputs
-// like k_fill_tma, so the tile stores of one group drain while the next
-// group's products run.  Lanes of a warp are rows 512 apart, so the tile store
-// goes through a 3D tensor map (columns, j, p).  The start states never reach
-// global memory; each lane keeps its own in a shared-memory slot for the rare
-// exact redo of a double row.
+// A chunk of 512 P streams (P a power of two, at least 32) whose first P
+// streams, the parents, are given: stream p + P j starts at P_0[j] parent_p,
+// with P_0[j] = T^(2^d P j) the level-0 power set of the distance 2^d P
+// (Sec. 5, 6).  A CTA takes one j: it builds the Four-Russians tables of
+// P_0[j] once, and the lanes of each warp are 32 consecutive parents, hence
+// 32 consecutive streams (rows p0 + P j ..), written by 2D tile stores like
+// k_fill_tma.  The start states never reach global memory.  A warp takes
+// FS_GROUPS groups of 32 parents in turn, so the tile stores of one group
+// drain while the next group's products run, and keeps a lane's start state
+// in a shared-memory slot for the rare exact redo of a double row.  Only rows
+// of at most FILL_SHORT_TILES tiles come here: for longer rows the start
+// states are a small part of the work, and a state table followed by the
+// fill's own configuration (many small CTAs for the exact doubles, which a
+// resident 32 KB table rules out) measured faster.
 constexpr int FS_WARPS = 8;
 constexpr int FS_NBUF = 2;
 constexpr int FS_GROUPS = 4;  // groups of 32 parents per warp, one after another
-constexpr int FS_CHILDREN = PSET_SIZE;  // streams per parent
+constexpr int FS_CHILDREN = PSET_SIZE;  // streams per parent (j < 512)
 
 template <int V>
 struct FuseCfg {
@@ -37,7 +40,7 @@ struct FuseCfg {
 template <int V, int DT>
 __global__ void __launch_bounds__(FS_WARPS * 32)
     k_fill_streams(const __grid_constant__ CUtensorMap map, const u32 *__restrict__ P0, const u32 *parents,
-                   size_t npar, size_t m, int *status)
+                   size_t npar, size_t m, int *status)  // npar = P
 {
     typedef Gen<V> G;
     typedef typename G::E E;
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(FS_WARPS * 32)
             fence_proxy_async_shared();
             __syncwarp();
             if (lane == 0) {
-                tma_store_3d(&map, tile, (int)j0, j, (int)p0);
+                tma_store_2d(&map, tile, (int)j0, (int)(p0 + npar * (size_t)j));
                 bulk_commit();
             }
         }
@@ -100,9 +103,9 @@ __global__ void __launch_bounds__(FS_WARPS * 32)
     if (lane == 0) bulk_wait_read<0>();
 }
 
-// npar parents (contiguous states) -> npar * 512 streams x m outputs in d_out
-// (stream-major).  cudaErrorNotSupported when the shape does not suit the
-// tile store (the caller then takes another path).
+// P = npar parents (contiguous states, P a power of two, at least 32) ->
+// 512 P streams x m outputs in d_out (stream-major), rows of at most
+// FILL_SHORT_TILES tiles.  cudaErrorNotSupported for other shapes.
 template <int V, int DT>
 cudaError_t launch_fill_streams_vd(const u32 *P0, const void *parents, size_t npar, size_t m, void *out,
                                    int *status, cudaStream_t stream, EncodeTiledFn encode)
@@ -110,17 +113,18 @@ cudaError_t launch_fill_streams_vd(const u32 *P0, const void *parents, size_t np
     constexpr int ES = (int)sizeof(typename OutElem<DT>::type);
     constexpr int COLS = 128 / ES;
     typedef FuseCfg<V> FC;
-    if (!encode || ((uintptr_t)out % 16) || ((m * ES) % 16) || m == 0 || m >= (1ull << 31) ||
-        npar >= (1ull << 31) || (size_t)FS_CHILDREN * m * ES >= (1ull << 40))
+    if (!encode || ((uintptr_t)out % 16) || ((m * ES) % 16) || m == 0 || (m + COLS - 1) / COLS > FILL_SHORT_TILES ||
+        npar < 32 ||
+        (npar & (npar - 1)) || (size_t)FS_CHILDREN * npar >= (1ull << 31) || m * ES >= (1ull << 40))
         return cudaErrorNotSupported;
     const size_t gy = (npar + FS_GROUPS * FS_WARPS * 32 - 1) / (FS_GROUPS * FS_WARPS * 32);
     if (gy > 65535) return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)m, (cuuint64_t)FS_CHILDREN, (cuuint64_t)npar};
-    const cuuint64_t strides[2] = {(cuuint64_t)(m * ES), (cuuint64_t)((size_t)FS_CHILDREN * m * ES)};
-    const cuuint32_t box[3] = {(cuuint32_t)COLS, 1u, 32u};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    if (encode(&map, ES == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, out, dims,
+    const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)(FS_CHILDREN * npar)};
+    const cuuint64_t strides[1] = {(cuuint64_t)(m * ES)};
+    const cuuint32_t box[2] = {(cuuint32_t)COLS, 32u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    if (encode(&map, ES == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, out, dims,
                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorNotSupported;

@@ -97,6 +97,9 @@ struct xr_ctx {
     cudaEvent_t ev_gen[2], ev_copy[2];
     xr::EncodeTiledFn encode;
     void *lazy_mutex;         // guards the lazy build of the large engines' tables
+    // power sets of further distances 2^d (index d < 256), built on first use
+    // by xr_fill_streams: the PSET_LEVELS level sets of that distance
+    uint32_t *dist_sets[xr::NUM_ENGINES_H][256];
 };
 
 namespace xr {
@@ -107,6 +110,10 @@ int ensure_engine(xr_ctx *ctx, int engine);
 int pset_index(int engine, int d);
 // The three level sets of distance index di of an engine.
 const uint32_t *pset_sets(const xr_ctx *ctx, int engine, int di);
+// The level-0 power set P_0[j] = T^(2^d j), j < 512, of any distance 2^d
+// (d < engine bits) of an engine with power sets, built and cached on first
+// use (the first use waits for the device); NULL on failure.
+const uint32_t *dist_sets(xr_ctx *ctx, int engine, int d);
 // Makes the context's device current for the duration of an entry point and
 // restores the caller's device afterwards (nothing to do when they agree), so
 // calls on contexts of different devices need no cudaSetDevice from the caller.

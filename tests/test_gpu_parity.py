@@ -344,6 +344,32 @@ def test_bulk_configuration_sampled(ctx, xr, name):
     assert ctx.status() == 0
 
 
+@pytest.mark.parametrize("name", ["xoshiro256**", "xoroshiro128+", "xoshiro128++"])
+def test_bulk_configuration_fused_sampled(ctx, xr, name):
+    """2^20 streams x 2^10 outputs from SplitMix64(42) through xr_fill_streams
+    (start states computed in the generating threads): 66 sampled streams and
+    the first 64 compared in full, native word and f64."""
+    import torch
+    c = W.CONFIG_BULK
+    S, m = c["S"], c["m"]
+    base = O.seed(name, c["seed"])
+    d = O.jump_log2(name, c["kind"])
+    idx = sorted(set(range(64)) | set(int(i) for i in W.sample_indices(S, 66, seed=3)))
+    d_base = ctx.empty_states(name, 1)
+    ctx.seed(name, c["seed"], d_base)
+    for dtype in (xr.native_dtype(name), "f64"):
+        out = ctx.empty_output(S * m, dtype)
+        ctx.fill_streams(name, c["kind"], d_base, 0, S, m, dtype, out)
+        torch.cuda.synchronize()
+        rows = out.view(S, m)[torch.as_tensor(idx, device="cuda")]
+        got = out_to_numpy(rows.contiguous(), dtype).reshape(len(idx), m)
+        for r, i in enumerate(idx):
+            raw, _ = O.generate(name, O.jump_pow(name, d, int(i), base), m)
+            assert_bits_equal(got[r], expected(name, raw, dtype), "%s %s stream %d" % (name, dtype, i))
+        del out
+    assert ctx.status() == 0
+
+
 @pytest.mark.parametrize("kind", ["jump", "long"])
 def test_jumpstart_configuration_sampled(ctx, xr, kind):
     """2^24 xoshiro256++ streams J^i(s0) / L^i(s0), 64 outputs each: 4096
@@ -373,11 +399,15 @@ def test_jumpstart_configuration_sampled(ctx, xr, kind):
         assert_bits_equal(rows[r], raw, "stream %d" % i)
 
 
-# (S, first, m): one stream; below one parent; one parent; parent + tail; a
-# high first with a tail; a row length the tile store cannot take (state
-# table path); two CTA rows of parents (8 warps x 32 parents each) + a tail
-FILL_STREAMS_CASES = [(1, 0, 16), (511, 3, 8), (512, 0, 64), (513, 7, 64), (3 * 512 + 100, 2**40 + 1, 24),
-                      (1024, 5, 5), (2 * 256 * 512 + 3, 11, 4)]
+# (S, first, m).  Below 512 x 32 streams everything goes through a state
+# table; from there on chunks of 512 P streams (P a power of two) take the
+# fused kernels.  Cases: tiny; below one chunk; a row length the tile store
+# cannot take; one chunk (P = 32); a chunk + a tail; two chunks (P = 64, 32)
+# + a tail with a high first; one chunk of P = 512 + a tail; long rows (the
+# kernel that reuses its table memory as tiles) with a tail, and P = 64.
+FILL_STREAMS_CASES = [(1, 0, 16), (513, 7, 64), (1024, 5, 5), (16384, 0, 64), (16384 + 5, 7, 64),
+                      (3 * 16384 + 100, 2**40 + 1, 24), (2 * 256 * 512 + 3, 11, 4), (16384 + 3, 9, 1000),
+                      (2 * 16384, 0, 520)]
 
 
 @pytest.mark.parametrize("name", ["xoshiro256++", "xoroshiro128**", "xoroshiro128++", "xoshiro128**",
