@@ -113,10 +113,9 @@ cudaError_t launch_fill_streams_vd(const u32 *P0, const void *parents, size_t np
     constexpr int ES = (int)sizeof(typename OutElem<DT>::type);
     constexpr int COLS = 128 / ES;
     typedef FuseCfg<V> FC;
-    if (!encode || ((uintptr_t)out % 16) || ((m * ES) % 16) || m == 0 || (m + COLS - 1) / COLS > FILL_SHORT_TILES ||
-        npar < 32 ||
-        (npar & (npar - 1)) || (size_t)FS_CHILDREN * npar >= (1ull << 31) || m * ES >= (1ull << 40))
-        return cudaErrorNotSupported;
+    const bool rows_ok = m > 0 && (m * ES) % 16 == 0 && (m + COLS - 1) / COLS <= (size_t)FILL_SHORT_TILES;
+    const bool parents_ok = npar >= 32 && (npar & (npar - 1)) == 0 && (size_t)FS_CHILDREN * npar < (1ull << 31);
+    if (!encode || ((uintptr_t)out % 16) || !rows_ok || !parents_ok) return cudaErrorNotSupported;
     const size_t gy = (npar + FS_GROUPS * FS_WARPS * 32 - 1) / (FS_GROUPS * FS_WARPS * 32);
     if (gy > 65535) return cudaErrorNotSupported;
     CUtensorMap map;
