@@ -502,6 +502,32 @@ def test_invalid_arguments(ctx, xr):
         ctx.fill("xoshiro256**", t, 1, 17, "u64", out)   # buffer too small
 
 
+def test_fill_streams_invalid_arguments(ctx, xr):
+    """xr_fill_streams rejects a dtype the generator does not have, an output
+    not aligned to its element size, a misaligned base state and an unknown
+    jump kind, and writes nothing; S = 0 and m = 0 are no-ops."""
+    import ctypes
+    import torch
+    lib, h = xr.lib(), ctx.handle
+    v = xr.VARIANTS["xoshiro256**"]
+    base = ctx.empty_states("xoshiro256**", 2)
+    ctx.seed("xoshiro256**", 1, base)
+    out = torch.full((1024 + 16,), 7, dtype=torch.uint8, device="cuda")
+    p, b = out.data_ptr(), base.data_ptr()
+    u64, u32 = xr.DTYPES["u64"], xr.DTYPES["u32"]
+    call = lambda kind, dt, base_ptr, out_ptr, S, m: lib.xr_fill_streams(h, v, kind, ctypes.c_void_p(base_ptr), 0, S, m,
+                                                                         dt, ctypes.c_void_p(out_ptr), None)
+    assert call(xr.KINDS["jump"], u32, b, p, 4, 16) == xr.XR_EINVAL       # no u32 outputs for a 64-bit generator
+    assert call(xr.KINDS["jump"], u64, b, p + 4, 4, 16) == xr.XR_EINVAL   # output not 8-byte aligned
+    assert call(xr.KINDS["jump"], u64, b + 8, p, 4, 16) == xr.XR_EINVAL   # state not 16-byte aligned
+    assert call(7, u64, b, p, 4, 16) == xr.XR_EINVAL                      # no such jump kind
+    assert call(xr.KINDS["jump"], u64, b, p, 0, 16) == xr.XR_OK
+    assert call(xr.KINDS["jump"], u64, b, p, 4, 0) == xr.XR_OK
+    torch.cuda.synchronize()
+    assert (out == 7).all()
+    assert ctx.status() == 0
+
+
 # ------------------------------------------------------------------ small outputs inside rows
 
 def _state_before(name, target, k):
