@@ -19,13 +19,16 @@ namespace xr {
 // k_fill_tma.  The start states never reach global memory.  A warp takes
 // FS_GROUPS groups of 32 parents in turn, so the tile stores of one group
 // drain while the next group's products run, and keeps a lane's start state
-// in a shared-memory slot for the rare exact redo of a double row.  Only rows
+// in a shared-memory slot for the rare exact redo of a double row.  One tile
+// per warp and 16 warps per CTA measured best (2^24 x 64: against 8 warps x
+// 2 tiles, u64 -6 %, f64 -4 %): shared memory, not the store queue, limits
+// the warps per SM.  Only rows
 // of at most FILL_SHORT_TILES tiles come here: for longer rows the start
 // states are a small part of the work, and a state table followed by the
 // fill's own configuration (many small CTAs for the exact doubles, which a
 // resident 32 KB table rules out) measured faster.
-constexpr int FS_WARPS = 8;
-constexpr int FS_NBUF = 2;
+constexpr int FS_WARPS = 16;
+constexpr int FS_NBUF = 1;
 constexpr int FS_GROUPS = 4;  // groups of 32 parents per warp, one after another
 constexpr int FS_CHILDREN = PSET_SIZE;  // streams per parent (j < 512)
 
