@@ -208,7 +208,9 @@ int xr_fill(xr_ctx *ctx, int variant, void *d_states, size_t S, size_t m, int dt
  *     states for a chunk, S states on the state-table path); not safe to call
  *     concurrently with xr_fill_seq or another xr_fill_streams on the same
  *     context.
- *   - XR_EINVAL for bad arguments; S = 0 or m = 0 is a valid no-op. */
+ *   - XR_EINVAL for bad arguments, and when the last stream index
+ *     first + S - 1 does not fit in 64 bits; S = 0 or m = 0 is a valid
+ *     no-op. */
 int xr_fill_streams(xr_ctx *ctx, int variant, int kind, const void *d_base, uint64_t first, size_t S, size_t m,
                     int dtype, void *d_out, void *stream);
 
@@ -250,7 +252,8 @@ int xr_fill_seq_noalloc(xr_ctx *ctx, int variant, void *d_state, size_t n, int d
  * (stream-major) and copies them to h_out (host, S * m elements of dtype;
  * page-locked memory gives full copy speed).  Generation and device-to-host
  * copies overlap through two staging buffers the context owns.  Blocks until
- * h_out is complete. */
+ * h_out is complete.  XR_EINVAL for bad arguments and when the last stream
+ * index first + S - 1 does not fit in 64 bits. */
 int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_base, uint64_t first,
                  size_t S, size_t m, int dtype, void *h_out, void *stream);
 

@@ -557,6 +557,7 @@ extern "C" int xr_fill_streams(xr_ctx *ctx, int variant, int kind, const void *d
     if (S == 0 || m == 0) return XR_OK;
     const size_t es = (size_t)xr_dtype_bytes(dtype);
     if (!states_ok(d_base) || !d_out || ((uintptr_t)d_out % es) || m > (SIZE_MAX / es) / S) return XR_EINVAL;
+    if (first > UINT64_MAX - (S - 1)) return XR_EINVAL;  // stream indices first .. first + S - 1 in 64 bits
     {
         const int erc = ensure_engine(ctx, engine_of(variant));
         if (erc != XR_OK) return erc;
@@ -648,6 +649,7 @@ extern "C" int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_ba
     if (!h_out) return XR_EINVAL;
     const size_t es = (size_t)xr_dtype_bytes(dtype);
     if (m > (SIZE_MAX / es) / S) return XR_EINVAL;
+    if (first > UINT64_MAX - (S - 1)) return XR_EINVAL;  // stream indices first .. first + S - 1 in 64 bits
     const size_t sb = (size_t)xr_state_bytes(variant);
     unsigned char any = 0;
     for (size_t b = 0; b < sb; ++b) any |= ((const unsigned char *)h_base)[b];

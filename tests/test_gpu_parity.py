@@ -523,8 +523,19 @@ def test_fill_streams_invalid_arguments(ctx, xr):
     assert call(7, u64, b, p, 4, 16) == xr.XR_EINVAL                      # no such jump kind
     assert call(xr.KINDS["jump"], u64, b, p, 0, 16) == xr.XR_OK
     assert call(xr.KINDS["jump"], u64, b, p, 4, 0) == xr.XR_OK
+    # stream indices first .. first + S - 1 must fit in 64 bits (the last one may be 2^64 - 1)
+    last = lambda first, S: lib.xr_fill_streams(h, v, xr.KINDS["jump"], ctypes.c_void_p(b), first, S, 16, u64,
+                                                ctypes.c_void_p(p), None)
+    assert last(2**64 - 3, 4) == xr.XR_EINVAL
+    assert last(2**64 - 4, 4) == xr.XR_OK
     torch.cuda.synchronize()
-    assert (out == 7).all()
+    assert (out[512:] == 7).all()   # the last call wrote its 4 x 16 u64 and nothing past them
+    want = O.bulk_fill("xoshiro256**", "jump", O.seed("xoshiro256**", 1), 4, 16, first=2**64 - 4).reshape(-1)
+    assert_bits_equal(out[:512].cpu().numpy().view(np.uint64), want, "streams 2^64 - 4 .. 2^64 - 1")
+    host = np.zeros(4 * 16, dtype=np.uint64)
+    hb = np.frombuffer(base.cpu().numpy().tobytes()[:32], dtype=np.uint8).copy()
+    assert lib.xr_fill_host(h, v, xr.KINDS["jump"], hb.ctypes.data_as(ctypes.c_void_p), 2**64 - 3, 4, 16, u64,
+                            host.ctypes.data_as(ctypes.c_void_p), None) == xr.XR_EINVAL
     assert ctx.status() == 0
 
 
