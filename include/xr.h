@@ -169,7 +169,13 @@ int xr_advance(xr_ctx *ctx, int variant, void *d_states, size_t count, uint64_t 
  *   d_states_out[i] = J^(first + i)(d_base),  i = 0 .. S-1,
  * where J is the jump (or long jump): stream 0 is the base after `first`
  * jumps, each next stream one jump further.  d_base (one state) is read only;
- * it may not overlap d_states_out. */
+ * it may not overlap d_states_out.
+ *   - For S of at least 512 x 32 streams (engines of at most 256 bits) the
+ *     first call that needs the power set of a new distance 2^J P (P the
+ *     largest power of two with 512 P <= S) builds and keeps it in the context
+ *     (cudaMalloc, 12 MiB for 256-bit states) and waits for the device once;
+ *     under stream capture it is not built and the call takes a slower path
+ *     with the same results. */
 int xr_make_streams(xr_ctx *ctx, int variant, int kind, const void *d_base, uint64_t first,
                     size_t S, void *d_states_out, void *stream);
 

@@ -261,6 +261,16 @@ const uint32_t *dist_sets(xr_ctx *ctx, int engine, int d)
     __atomic_store_n(&ctx->dist_sets[engine][d], p, __ATOMIC_RELEASE);
     return p;
 }
+
+const uint32_t *dist_sets_outside_capture(xr_ctx *ctx, int engine, int d, cudaStream_t st)
+{
+    if (engine >= NUM_PSET_ENGINES || d < 0 || d >= engine_bits(engine)) return nullptr;
+    uint32_t *p = __atomic_load_n(&ctx->dist_sets[engine][d], __ATOMIC_ACQUIRE);
+    if (p) return p;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    return dist_sets(ctx, engine, d);
+}
 }  // namespace xr
 
 extern "C" int xr_ctx_destroy(xr_ctx *ctx)
@@ -448,14 +458,38 @@ extern "C" int xr_advance(xr_ctx *ctx, int variant, void *d_states, size_t count
                                       count, (cudaStream_t)stream));
 }
 
-// out[i] = (T^(2^d))^(first + i) base for i < S.
+// out[i] = (T^(2^d))^(first + i) base for i < S.  With `cached`, a chunk of
+// 512 P streams (P the largest power of two, at least 32, that fits) takes
+// its P parents from the path below and its other streams p + P j from one
+// launch over the level-0 power set of the distance 2^d P (built once and
+// kept in the context; not built under stream capture), whose warps load
+// and store contiguous states; the rest of the range follows the same way.
+// Callers that must not allocate pass cached = false.
 static cudaError_t make_streams(xr_ctx *ctx, int variant, int d, const void *d_base, uint64_t first,
-                                size_t S, void *out, cudaStream_t st)
+                                size_t S, void *out, cudaStream_t st, bool cached = true)
 {
     if (S == 0) return cudaSuccess;
     const int e = engine_of(variant);
     const int di = pset_index(e, d);
     cudaError_t err;
+    if (cached && e < NUM_PSET_ENGINES && S >= (size_t)PSET_SIZE * 32 && first <= UINT64_MAX - (S - 1)) {
+        size_t P = 32;
+        int k = 5;
+        while (P * 2 * PSET_SIZE <= S) {
+            P *= 2;
+            ++k;
+        }
+        const uint32_t *Q = dist_sets_outside_capture(ctx, e, (d + k) % engine_bits(e), st);
+        if (Q) {
+            const size_t sb = (size_t)xr_state_bytes(variant), chunk = P * PSET_SIZE;
+            err = make_streams(ctx, variant, d, d_base, first, P, out, st, false);
+            if (err == cudaSuccess) err = launch_streams_jmajor(e, Q, out, P, st);
+            if (err == cudaSuccess && S > chunk)
+                err = make_streams(ctx, variant, d, d_base, first + chunk, S - chunk, (char *)out + chunk * sb, st,
+                                   true);
+            return err;
+        }
+    }
     if (first && di >= 0) {
         // J^first(base) by one warp from the power sets of this distance
         err = launch_warp_jump(e, pset_sets(ctx, e, di), ctx->tables[e], d, d_base, out, first, st);
@@ -625,7 +659,7 @@ extern "C" int xr_fill_seq(xr_ctx *ctx, int variant, void *d_state, size_t n, in
     ctx->scratch_bytes = cap;
     if (err != cudaSuccess) return status_of(err);
     // segment p starts at T^(p * 2^SEQ_LOG2) s
-    err = make_streams(ctx, variant, SEQ_LOG2, d_state, 0, P, ctx->scratch, st);
+    err = make_streams(ctx, variant, SEQ_LOG2, d_state, 0, P, ctx->scratch, st, false);
     if (err == cudaSuccess && full)
         err = launch_fill(variant, dtype, XR_STREAM_MAJOR, ctx->scratch, full, seg, seg, d_out, 1,
                           ctx->d_status, st, ctx->encode);
@@ -756,7 +790,7 @@ extern "C" int xr_fill_seq_noalloc(xr_ctx *ctx, int variant, void *d_state, size
     // Every slot read below is written first in this call (make_streams fills
     // slots 0 .. P-1: the base copy, then the stream starts), so nothing has
     // to start at zero.
-    cudaError_t err = make_streams(ctx, variant, SEQ_LOG2_NOALLOC, d_state, 0, P, scratch, st);
+    cudaError_t err = make_streams(ctx, variant, SEQ_LOG2_NOALLOC, d_state, 0, P, scratch, st, false);
     if (err == cudaSuccess && full)
         err = launch_fill(variant, dtype, XR_STREAM_MAJOR, scratch, full, seg, seg, d_out, 1,
                           ctx->d_status, st, ctx->encode);

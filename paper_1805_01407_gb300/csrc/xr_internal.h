@@ -65,6 +65,9 @@ cudaError_t launch_build_power_sets(int engine, const uint32_t *tables, const in
 // with states[i] = (T^(2^d))^i states[0], sets3 = the three sets of distance d.
 cudaError_t launch_streams_psets(int engine, const uint32_t *sets3, void *states, size_t S,
                                  cudaStream_t stream);
+// Given states[0 .. P-1], fill states[P .. 512 P - 1] with
+// states[p + P j] = Q_j states[p], Q = the level-0 power set of distance 2^d P.
+cudaError_t launch_streams_jmajor(int engine, const uint32_t *Q, void *states, size_t P, cudaStream_t stream);
 // out = (T^(2^d))^e base by one warp through the three power sets of distance
 // 2^d (engines with power sets only: 256, 128 or 64 state bits).
 cudaError_t launch_warp_jump(int engine, const uint32_t *psets_d, const uint32_t *tables, int d, const void *base,
@@ -114,6 +117,9 @@ const uint32_t *pset_sets(const xr_ctx *ctx, int engine, int di);
 // (d < engine bits) of an engine with power sets, built and cached on first
 // use (the first use waits for the device); NULL on failure.
 const uint32_t *dist_sets(xr_ctx *ctx, int engine, int d);
+// The same when already built; otherwise built now unless `st` is capturing
+// (NULL then, and nothing is built).
+const uint32_t *dist_sets_outside_capture(xr_ctx *ctx, int engine, int d, cudaStream_t st);
 // Makes the context's device current for the duration of an entry point and
 // restores the caller's device afterwards (nothing to do when they agree), so
 // calls on contexts of different devices need no cudaSetDevice from the caller.

@@ -403,6 +403,44 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Children of a chunk whose first P streams (the parents) are in place:
+// states[p + P j] = Q_j states[p] for j = 1 .. 511, with Q_j = T^(2^d P j) the
+// level-0 power set of the distance 2^d P.  The CTA shares j (its tables in
+// shared memory) and its lanes take consecutive parents, so the parent loads
+// and the child stores of a warp are contiguous.
+template <int NW>
+__global__ void __launch_bounds__(256) k_streams_jmajor(const u32 *__restrict__ Q, u32 *states, size_t P)
+{
+    typedef Russians<NW> RT;
+    __shared__ __align__(16) u32 T[RT::WORDS];
+    const int j = blockIdx.y + 1;
+    russians_build<NW>(Q + (size_t)j * RT::n * NW, T);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < STREAMS_PER_THREAD; ++k) {
+        const size_t p = ((size_t)blockIdx.x * STREAMS_PER_THREAD + k) * blockDim.x + threadIdx.x;
+        if (p >= P) return;
+        u32 v[NW], r[NW];
+        load_vec<NW>(v, states + p * NW);
+        russians_matvec<NW>(T, v, r);
+        store_vec<NW>(r, states + (p + P * (size_t)j) * NW);
+    }
+}
+
+cudaError_t launch_streams_jmajor(int engine, const uint32_t *Q, void *states, size_t P, cudaStream_t stream)
+{
+    const size_t per_cta = (size_t)256 * STREAMS_PER_THREAD;
+    const dim3 grid((unsigned)((P + per_cta - 1) / per_cta), PSET_SIZE - 1);
+    switch (engine_bits(engine)) {
+    case 256: k_streams_jmajor<8><<<grid, 256, 0, stream>>>(Q, (u32 *)states, P); break;
+    case 128: k_streams_jmajor<4><<<grid, 256, 0, stream>>>(Q, (u32 *)states, P); break;
+    case 64: k_streams_jmajor<2><<<grid, 256, 0, stream>>>(Q, (u32 *)states, P); break;
+    default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_streams_psets(int engine, const uint32_t *sets3, void *states, size_t S,
                                  cudaStream_t stream)
 {
