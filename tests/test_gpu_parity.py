@@ -248,11 +248,11 @@ def test_make_streams_chunked(ctx, xr, name, kind):
     """From 512 x 32 streams on, a chunk of 512 P streams takes its streams
     p + P j from one launch over the power set of the distance 2^J P; the rest
     of the range follows.  One chunk (P = 32); a chunk and a rest below it;
-    two chunks (P = 64, then 32) and a rest, from a nonzero first: every
-    state against one jump after another."""
+    two chunks (P = 64, then 32) and a rest, from a nonzero first; a chunk
+    ending at stream 2^64 - 1: every state against one jump after another."""
     base = O.seed(name, 5)
     d_base = states_to_device(name, base[None, :])
-    for S, first in ((16384, 0), (16384 + 77, 3), (3 * 16384 + 5, 1000)):
+    for S, first in ((16384, 0), (16384 + 77, 3), (3 * 16384 + 5, 1000), (16384, 2**64 - 16384)):
         out = ctx.empty_states(name, S)
         ctx.make_streams(name, kind, d_base, first, S, out)
         got = states_from_device(name, out)
