@@ -208,8 +208,10 @@ int xr_fill(xr_ctx *ctx, int variant, void *d_states, size_t S, size_t m, int dt
  *     same results.
  *   - The first call that needs the power set of a new distance 2^J P builds
  *     and keeps it in the context (3 x 512 matrices: 12 MiB for 256-bit
- *     states, with cudaMalloc) and waits for the device once; so does a call
- *     that grows the scratch.  Make such first calls outside stream capture.
+ *     states, with cudaMalloc) and waits for the device once; under stream
+ *     capture it is not built and those streams take the state table.  A call
+ *     that grows the scratch waits for the device too: make first calls
+ *     outside stream capture.
  *   - Uses the context scratch (grown with cudaMalloc when too small: P
  *     states for a chunk, S states on the state-table path); not safe to call
  *     concurrently with xr_fill_seq or another xr_fill_streams on the same

@@ -555,8 +555,10 @@ static cudaError_t fill_streams(xr_ctx *ctx, int variant, int d, const void *d_b
                 P *= 2;
                 ++k;
             }
-            const uint32_t *Q = dist_sets(ctx, e, (d + k) % n);
-            if (!Q) return cudaErrorMemoryAllocation;
+            // not built under stream capture (or if building fails): the rest
+            // of the range then takes the state table
+            const uint32_t *Q = dist_sets_outside_capture(ctx, e, (d + k) % n, st);
+            if (!Q) break;
             size_t cap = ctx->scratch_bytes;
             err = ensure(&ctx->scratch, &cap, P * sb);
             ctx->scratch_bytes = cap;
