@@ -95,6 +95,24 @@ def test_successive_jumps_equal_one_power(name):
     assert (O.streams(name, "jump", s, 10, first=30) == st[30:40]).all()
 
 
+@pytest.mark.parametrize("name", ["xoshiro256++", "xoroshiro128**", "xoroshiro128++", "xoshiro128**", "xoroshiro64*"])
+@pytest.mark.parametrize("kind", ["jump", "long"])
+def test_chunk_decomposition_of_streams(name, kind):
+    """Stream p + P j of a range equals j jumps of distance 2^(J + log2 P)
+    applied to stream p (P a power of two): the reading behind chunks of 512 P
+    streams, whose streams are taken from P parents with the power set of
+    that distance.  Distances past the state size wrap (T^(2^n) = T)."""
+    s = O.seed(name, 13)
+    d = O.jump_log2(name, kind)
+    n = O.state_bits(name)
+    for k in (5, 6, 15, 70):
+        P = 1 << k
+        for p, j in ((0, 1), (3, 2), (P - 1, 511), (17 % P, 300)):
+            stream = O.jump_pow(name, d, p + P * j, s)
+            parent = O.jump_pow(name, d, p, s)
+            assert (stream == O.jump_pow(name, (d + k) % n, j, parent)).all(), (k, p, j)
+
+
 def test_long_jump_is_a_power_of_the_jump():
     """2^192 = 2^64 * 2^128 and 2^96 = 2^32 * 2^64."""
     for name, ratio in (("xoshiro256**", 2**64), ("xoroshiro128++", 2**32)):
