@@ -44,14 +44,14 @@ def native_dtype(variant: str) -> str:
 
 
 def sample_indices(S: int, count: int, seed: int) -> np.ndarray:
-    """Sorted distinct stream indices in [0, S): 0 and S-1 plus uniform draws."""
+    """count sorted distinct stream indices in [0, S): 0 and S-1 plus
+    count - 2 uniform draws without replacement from the indices between."""
     rng = np.random.default_rng(seed)
     if count >= S:
         return np.arange(S, dtype=np.int64)
-    idx = set([0, S - 1])
-    while len(idx) < count:
-        idx.update(int(x) for x in rng.integers(0, S, size=count))
-    return np.array(sorted(idx)[:count], dtype=np.int64)
+    inner = rng.choice(S - 2, size=max(count - 2, 0), replace=False) + 1 if count > 2 else np.zeros(0, np.int64)
+    idx = np.concatenate([[0, S - 1], inner])[:count]
+    return np.sort(idx.astype(np.int64))
 
 
 # (S, m) shapes for element-by-element parity: single values, partial tiles,
