@@ -539,7 +539,6 @@ static cudaError_t fill_streams(xr_ctx *ctx, int variant, int d, const void *d_b
     const int e = engine_of(variant);
     const int n = engine_bits(e);
     const size_t sb = (size_t)xr_state_bytes(variant), es = (size_t)xr_dtype_bytes(dtype);
-    // what the tile store needs (the launcher checks the same)
     // short rows (at most 4 tiles of 128 bytes) that the tile store can take;
     // the launcher checks the same
     const bool tiles_ok = ctx->encode && ((uintptr_t)out % 16) == 0 && ((m * es) % 16) == 0 && m * es <= 512 &&
