@@ -7,6 +7,7 @@ equidistribution statements on tiny engines of Sec. 7, primitivity (Sec. 6),
 the prose restatements of the scrambler parameters (Sec. 10), and exact
 rational arithmetic for the doubles (Sec. 5.3).
 """
+import os
 import random
 from fractions import Fraction
 
@@ -466,9 +467,10 @@ def test_output_precedes_update():
 # --------------------------------------------------------------- SplitMix64 (parity unpinned)
 
 def test_splitmix64_properties():
-    """SplitMix64's constants are not printed in the paper (parity unpinned).  What
-    is checked: 32-bit states take the low half of each output first, and the
-    outputs of a seed are distinct (the mixer is a bijection of a Weyl sequence)."""
+    """Word layout of the seeding (Sec. 5.3): 32-bit states take the low half of
+    each SplitMix64 output first, 64-bit states take consecutive outputs, and
+    the outputs of a seed are distinct (the mixer is a bijection of a Weyl
+    sequence).  The constants are pinned by the next test."""
     z = O.splitmix64(42, 2)
     s = O.seed("xoshiro128++", 42)
     assert [int(x) for x in s] == [int(z[0]) & 0xffffffff, int(z[0]) >> 32,
@@ -477,6 +479,75 @@ def test_splitmix64_properties():
     assert (O.seed("xoroshiro128+", 42) == O.splitmix64(42, 2)).all()
     many = O.splitmix64(0, 1 << 16)
     assert len(set(int(x) for x in many)) == 1 << 16
+
+
+def _golden_gamma():
+    """The odd 64-bit integer nearest 2^64 / phi, phi the golden ratio, from an
+    exact integer square root: 2^64 (sqrt 5 - 1) / 2 = (sqrt(5 * 2^256) - 2^128) / 2^65."""
+    import math
+    x = (math.isqrt(5 << 256) - (1 << 128)) >> 65     # floor(2^64 / phi)
+    return x if x & 1 else x + 1
+
+
+def _independent_mix64(tmp_path):
+    """The 64-bit SplitMix finalizer as an independent project defines it:
+    pybind11 carries it in pybind11/detail/internals.h as `mix64` (its comment
+    names it David Stafford's variant 13 of the MurmurHash3 finalizer, the
+    one SplitMix popularized).  The header is compiled into a one-function
+    shared object and called; nothing of it is copied here."""
+    import ctypes
+    import shutil
+    import subprocess
+    import sysconfig
+    try:
+        import pybind11
+        inc = pybind11.get_include()
+    except ImportError:
+        pytest.skip("pybind11 headers not installed")
+    pyinc = sysconfig.get_paths()["include"]
+    gxx = shutil.which("g++")
+    if not gxx or not os.path.exists(os.path.join(inc, "pybind11", "detail", "internals.h")) \
+            or not os.path.exists(os.path.join(pyinc, "Python.h")):
+        pytest.skip("g++, pybind11's internals.h or Python.h missing")
+    src = tmp_path / "mix.cpp"
+    src.write_text('#include <pybind11/detail/internals.h>\n'
+                   'extern "C" unsigned long long ext_mix64(unsigned long long z)\n'
+                   '{ return pybind11::detail::mix64(z); }\n')
+    so = tmp_path / "mix.so"
+    subprocess.run([gxx, "-O1", "-std=c++17", "-fPIC", "-shared", "-w", "-I" + inc, "-I" + pyinc, str(src),
+                    "-o", str(so)], check=True)
+    lib = ctypes.CDLL(str(so))
+    lib.ext_mix64.restype = ctypes.c_ulonglong
+    lib.ext_mix64.argtypes = [ctypes.c_ulonglong]
+    return lib.ext_mix64
+
+
+def test_splitmix64_against_golden_gamma_and_independent_mixer(tmp_path):
+    """Sec. 5.3 names SplitMix but does not define it.  Output i of the oracle's
+    SplitMix64(seed) must be the finalizer applied to seed + (i + 1) gamma
+    (mod 2^64): a Weyl sequence whose increment is the golden-ratio gamma,
+    derived here from phi, and whose outputs go through the variant-13
+    finalizer, taken from an independent implementation in this environment.
+    A changed multiplier, shift or increment, or mixing before the increment,
+    fails this test."""
+    gamma = _golden_gamma()
+    assert gamma == 0x9E3779B97F4A7C15
+    mix64 = _independent_mix64(tmp_path)
+    rng = random.Random(55)
+    M = (1 << 64) - 1
+    seeds = [0, 1, 42, 0x0123456789ABCDEF, M, 1 << 63] + [rng.getrandbits(64) for _ in range(200)]
+    for seed in seeds:
+        got = [int(x) for x in O.splitmix64(seed, 6)]
+        want = [mix64((seed + (i + 1) * gamma) & M) for i in range(6)]
+        assert got == want, hex(seed)
+    # the seeding of every word size follows those outputs
+    for name in ("xoshiro256**", "xoroshiro128++", "xoshiro512+", "xoroshiro1024**"):
+        k = O.state_words(name)
+        assert [int(x) for x in O.seed(name, 42)] == [mix64((42 + (i + 1) * gamma) & M) for i in range(k)]
+    z = [mix64((42 + (i + 1) * gamma) & M) for i in range(2)]
+    assert [int(x) for x in O.seed("xoshiro128**", 42)] == [z[0] & 0xffffffff, z[0] >> 32,
+                                                            z[1] & 0xffffffff, z[1] >> 32]
+    assert [int(x) for x in O.seed("xoroshiro64*", 42)] == [z[0] & 0xffffffff, z[0] >> 32]
 
 
 def test_bulk_fill_equals_streams_then_fill():
