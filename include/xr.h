@@ -127,15 +127,23 @@ int xr_ctx_create(int device, xr_ctx **out);
  * accepted. */
 int xr_ctx_destroy(xr_ctx *ctx);
 
-/* ---- properties (pure host functions, no GPU needed) -------------------- */
+/* ---- properties (pure host functions, no GPU needed) --------------------
+ * State size k words of w bits (n = k w) of each engine, from its definition:
+ * Sec. 3.1 (xoroshiro, k = 2 or 16), Sec. 3.2 (xoshiro, k = 4 or 8), Table 4
+ * (w = 64) and Table 7 (w = 32). */
 int xr_state_words(int variant);      /* 2 .. 16; -1 for a bad variant */
 int xr_word_bits(int variant);        /* 64 or 32; -1 for a bad variant */
 int xr_state_bytes(int variant);      /* 8 .. 128; -1 for a bad variant */
 int xr_state_bits(int variant);       /* n = 64 .. 1024; -1 for a bad variant */
-int xr_dtype_bytes(int dtype);        /* 8, 4, 8, 4; -1 for a bad dtype */
-const char *xr_variant_name(int variant);  /* e.g. "xoshiro256**"; NULL if bad */
-const char *xr_error_string(int status);   /* never NULL */
-/* log2 of the jump distance of `kind` for `variant`; -1 if bad. */
+/* Bytes of one output value: 8, 4, 8, 4 for u64, u32, f64, f32 (Sec. 5.3
+ * for the floating-point values); -1 for a bad dtype. */
+int xr_dtype_bytes(int dtype);
+/* Name of a generator as in Tables 5 and 8, e.g. "xoshiro256**"; NULL if bad. */
+const char *xr_variant_name(int variant);
+const char *xr_error_string(int status);   /* never NULL; no counterpart in the paper */
+/* log2 of the jump distance of `kind` for `variant`; -1 if bad.  Sec. 5
+ * offers jumps but prints no distance; this library takes 2^(n/2) (jump) and
+ * 2^(3n/4) (long jump) for an n-bit state. */
 int xr_jump_log2(int variant, int kind);
 
 /* ---- seeding (Sec. 5.3) ---------------------------------------------------
@@ -148,6 +156,9 @@ int xr_seed_many(xr_ctx *ctx, int variant, const uint64_t *d_seeds, size_t count
                  void *d_states, void *stream);
 
 /* ---- state transfer ------------------------------------------------------
+ * The generator state is the whole checkpoint of a sequence; the captions of
+ * Figs. 1 to 4 require it not to be all zeros (the zero state is the one
+ * fixed point of a linear engine, Sec. 6).
  * xr_set_state copies one state from host words (h_words: state bytes, layout
  * as above) to d_state; rejects the all-zero state with XR_EZERO_STATE.
  * xr_get_state copies one state from d_state to h_words and waits on stream. */
@@ -165,7 +176,8 @@ int xr_jump(xr_ctx *ctx, int variant, int kind, void *d_states, size_t count, ui
 int xr_advance(xr_ctx *ctx, int variant, void *d_states, size_t count, uint64_t nsteps,
                void *stream);
 
-/* xr_make_streams: start states of S independent streams,
+/* xr_make_streams (Sec. 5, jumps; Sec. 6, jumping is a product with the
+ * matrix power T^J): start states of S independent streams,
  *   d_states_out[i] = J^(first + i)(d_base),  i = 0 .. S-1,
  * where J is the jump (or long jump): stream 0 is the base after `first`
  * jumps, each next stream one jump further.  d_base (one state) is read only;
@@ -181,7 +193,9 @@ int xr_make_streams(xr_ctx *ctx, int variant, int kind, const void *d_base, uint
 
 /* ---- generation ------------------------------------------------------------
  * xr_fill: S streams x m outputs.  Stream i starts at d_states[i] and emits
- * m outputs of next() (scramble, then step), converted to dtype, placed by
+ * m outputs of next() (Sec. 2: the output is the scrambler, Sec. 4, applied
+ * to the current state, then the engine of Sec. 3 steps the state; doubles
+ * and floats as in Sec. 5.3), converted to dtype, placed by
  * layout into d_out (S * m elements of dtype).  With write_back != 0 the
  * state after the m steps is written back to d_states[i], so a later call
  * continues each sequence.  S = 0 or m = 0 is a valid no-op (apart from
@@ -223,9 +237,11 @@ int xr_fill_streams(xr_ctx *ctx, int variant, int kind, const void *d_base, uint
                     int dtype, void *d_out, void *stream);
 
 /* xr_fill_seq: the first n outputs of one sequence starting at d_state, into
- * d_out (n elements of dtype); d_state is then advanced by n steps.  The
+ * d_out (n elements of dtype); d_state is then advanced by n steps (the n
+ * calls of next() of Sec. 2).  The
  * sequence is split into segments of 2^10 outputs whose start states are
- * T^(p * 2^10) s (jump-ahead), kept in the context's scratch memory, so the
+ * T^(p * 2^10) s (jump-ahead as a matrix power, Sec. 6), kept in the
+ * context's scratch memory, so the
  * whole GPU works on one sequence.  Not safe to call concurrently on two
  * streams with the same context (shared scratch). */
 int xr_fill_seq(xr_ctx *ctx, int variant, void *d_state, size_t n, int dtype, void *d_out,
@@ -238,11 +254,19 @@ int xr_fill_seq(xr_ctx *ctx, int variant, void *d_state, size_t n, int dtype, vo
  * or fail.  (The paper has no counterpart: this is a property of the
  * library, not of the method.)  The outputs and the advanced state are the
  * ones xr_fill_seq gives.
- *   - Allocates nothing: the segment start states live in one static device
- *     array of XR_NOALLOC_MAX_OUTPUTS / 1024 states x 32 bytes (2 MiB) that
- *     every GPU loading the library holds until the process exits.  The
- *     context (created earlier) supplies the jump tables.
- *   - n > XR_NOALLOC_MAX_OUTPUTS returns XR_EINVAL and enqueues nothing.
+ *   - Allocates nothing: the segment start states (one state per 1024
+ *     outputs) live in one static device array of XR_NOALLOC_SCRATCH_BYTES
+ *     (2 MiB) that every GPU loading the library holds until the process
+ *     exits.  The context (created earlier) supplies the jump tables.
+ *   - The largest n is XR_NOALLOC_MAX_OUTPUTS_FOR(state bytes): 2^26 outputs
+ *     for states of up to 32 bytes, 2^25 for xoshiro512 (64-byte states) and
+ *     2^24 for xoroshiro1024 (128-byte states).  A larger n returns XR_EINVAL
+ *     and enqueues nothing.
+ *   - The jump tables of xoshiro512 and xoroshiro1024 are built on first use,
+ *     which allocates; this call does not build them and returns
+ *     XR_EUNSUPPORTED until an earlier call on the same context has (any
+ *     call on that generator that jumps: xr_fill_seq, xr_jump, xr_advance,
+ *     xr_make_streams, xr_jump_table).
  *   - The first call on a device looks up the array's device address (with
  *     that device current, cudaGetSymbolAddress); make that first call
  *     before any stream capture.
@@ -251,7 +275,11 @@ int xr_fill_seq(xr_ctx *ctx, int variant, void *d_state, size_t n, int dtype, vo
  *     reads is written earlier in the same call.  Calls that overlap on the
  *     GPU (different streams, or different threads without ordering) race on
  *     the array and give wrong outputs: serialize them. */
+#define XR_NOALLOC_SCRATCH_BYTES ((size_t)2 << 20)
 #define XR_NOALLOC_MAX_OUTPUTS ((size_t)1 << 26)
+#define XR_NOALLOC_MAX_OUTPUTS_FOR(state_bytes)                                  \
+    ((size_t)(state_bytes) <= 32 ? XR_NOALLOC_MAX_OUTPUTS                        \
+                                 : (XR_NOALLOC_SCRATCH_BYTES / (size_t)(state_bytes)) << 10)
 int xr_fill_seq_noalloc(xr_ctx *ctx, int variant, void *d_state, size_t n, int dtype, void *d_out,
                         void *stream);
 
@@ -446,16 +474,19 @@ int xr_linear_complexity_many(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, 
 /* ---- status and inspection ------------------------------------------------ */
 
 /* Sticky device status: XR_OK, or the first error a kernel recorded
- * (XR_EZERO_STATE).  Waits for the device.  reset != 0 clears it. */
+ * (XR_EZERO_STATE: a kernel met the all-zero state, which a full-period
+ * linear engine never leaves or reaches from a nonzero state, Sec. 6).
+ * Waits for the device.  reset != 0 clears it. */
 int xr_status(xr_ctx *ctx, int reset);
 
-/* Copy the jump table entry T^(2^k) of variant's engine to h_out (host):
+/* Copy the jump table entry T^(2^k) of variant's engine (the F2 transition
+ * matrix T of Sec. 3 raised to 2^k, Sec. 6) to h_out (host):
  * n columns, column c = T^(2^k) e_c as n/32 uint32 words (bit r of the column
  * is bit r % 32 of word r / 32); n * n / 8 bytes.  Waits for the copy. */
 int xr_jump_table(xr_ctx *ctx, int variant, int k, void *h_out);
 
 /* Number of kernels this process has launched through libxr so far (all
- * contexts; a host-side counter, no GPU needed).  Lets a caller count the
+ * contexts; a host-side counter, no GPU needed; no counterpart in the paper).  Lets a caller count the
  * launches inside a timed region. */
 uint64_t xr_launch_count(void);
 

@@ -418,6 +418,7 @@ extern "C" int xr_linear_complexity_many(xr_ctx *ctx, const xr_lc_job *jobs, siz
 {
     if (!ctx || (njobs && (!jobs || !d_states || !d_scratch || !h_lc))) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_linear_complexity_many");
     if (njobs > (1u << 20) || ((uintptr_t)d_states % 16) || (state_stride % 16) ||
         ((uintptr_t)d_scratch % 16))
         return XR_EINVAL;
@@ -434,6 +435,7 @@ extern "C" int xr_linear_complexity(xr_ctx *ctx, int variant, int bit, size_t N,
 {
     if (!ctx || !d_state || !h_lc || !d_scratch) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_linear_complexity");
     xr_lc_job job;
     job.variant = variant;
     job.bit = bit;
@@ -452,6 +454,7 @@ extern "C" int xr_zeroland(xr_ctx *ctx, int variant, size_t nout, size_t window,
 {
     if (!ctx || variant < 0 || variant >= XR_NUM_VARIANTS || !d_counts) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_zeroland");
     if (window < 1 || window > 64 || nout < window || nout > ((size_t)1 << 32)) return XR_EINVAL;
     if ((uintptr_t)d_counts % 8) return XR_EINVAL;
     const cudaStream_t st = (cudaStream_t)stream;

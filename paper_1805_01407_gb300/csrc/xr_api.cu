@@ -328,7 +328,7 @@ extern "C" int xr_ctx_create(int device, xr_ctx **out)
     }
     if (rc == XR_OK) rc = status_of(cudaMalloc((void **)&ctx->d_status, sizeof(int)));
     if (rc == XR_OK) rc = status_of(cudaMemset(ctx->d_status, 0, sizeof(int)));
-    if (rc == XR_OK) rc = status_of(cudaMalloc(&ctx->base_state, 32));
+    if (rc == XR_OK) rc = status_of(cudaMalloc(&ctx->base_state, XR_MAX_STATE_BYTES));
     if (rc == XR_OK) rc = status_of(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
     for (int b = 0; b < 2 && rc == XR_OK; ++b) {
         rc = status_of(cudaEventCreateWithFlags(&ctx->ev_gen[b], cudaEventDisableTiming));
@@ -376,6 +376,7 @@ extern "C" int xr_seed(xr_ctx *ctx, int variant, uint64_t seed, void *d_state, v
 {
     if (!ctx || !variant_ok(variant) || !d_state || ((uintptr_t)d_state % 16)) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_seed");
     return status_of(launch_seed(variant, NULL, seed, 1, d_state, ctx->d_status, (cudaStream_t)stream));
 }
 
@@ -384,6 +385,7 @@ extern "C" int xr_seed_many(xr_ctx *ctx, int variant, const uint64_t *d_seeds, s
 {
     if (!ctx || !variant_ok(variant)) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_seed_many");
     if (count == 0) return XR_OK;
     if (!d_seeds || !d_states || ((uintptr_t)d_states % 16) || ((uintptr_t)d_seeds % 8))
         return XR_EINVAL;
@@ -431,6 +433,7 @@ extern "C" int xr_jump(xr_ctx *ctx, int variant, int kind, void *d_states, size_
 {
     if (!ctx || !variant_ok(variant) || (kind != XR_JUMP && kind != XR_LONG_JUMP)) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_jump");
     if (count == 0 || times == 0) return XR_OK;
     if (!states_ok(d_states)) return XR_EINVAL;
     {
@@ -447,6 +450,7 @@ extern "C" int xr_advance(xr_ctx *ctx, int variant, void *d_states, size_t count
 {
     if (!ctx || !variant_ok(variant)) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_advance");
     if (count == 0 || nsteps == 0) return XR_OK;
     if (!states_ok(d_states)) return XR_EINVAL;
     {
@@ -509,6 +513,7 @@ extern "C" int xr_make_streams(xr_ctx *ctx, int variant, int kind, const void *d
 {
     if (!ctx || !variant_ok(variant) || (kind != XR_JUMP && kind != XR_LONG_JUMP)) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_make_streams");
     if (S == 0) return XR_OK;
     if (!states_ok(d_base) || !states_ok(d_states_out)) return XR_EINVAL;
     const size_t sb = (size_t)xr_state_bytes(variant);
@@ -589,6 +594,7 @@ extern "C" int xr_fill_streams(xr_ctx *ctx, int variant, int kind, const void *d
     if (!ctx || !variant_ok(variant) || !dtype_ok(variant, dtype)) return XR_EINVAL;
     if (kind != XR_JUMP && kind != XR_LONG_JUMP) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_fill_streams");
     if (S == 0 || m == 0) return XR_OK;
     const size_t es = (size_t)xr_dtype_bytes(dtype);
     if (!states_ok(d_base) || !d_out || ((uintptr_t)d_out % es) || m > (SIZE_MAX / es) / S) return XR_EINVAL;
@@ -621,6 +627,7 @@ extern "C" int xr_fill(xr_ctx *ctx, int variant, void *d_states, size_t S, size_
 {
     if (!ctx || !fill_args_ok(variant, d_states, S, m, dtype, layout, d_out)) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_fill");
     if (S == 0 || m == 0) return XR_OK;
     return status_of(launch_fill(variant, dtype, layout, d_states, S, m, m, d_out, write_back,
                                  ctx->d_status, (cudaStream_t)stream, ctx->encode));
@@ -644,6 +651,7 @@ extern "C" int xr_fill_seq(xr_ctx *ctx, int variant, void *d_state, size_t n, in
 {
     if (!ctx || !variant_ok(variant) || !dtype_ok(variant, dtype)) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_fill_seq");
     if (n == 0) return XR_OK;
     const size_t es = (size_t)xr_dtype_bytes(dtype);
     if (!states_ok(d_state) || !d_out || ((uintptr_t)d_out % es)) return XR_EINVAL;
@@ -679,6 +687,7 @@ extern "C" int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_ba
 {
     if (!ctx || !variant_ok(variant) || !dtype_ok(variant, dtype) || !h_base) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
+    NvtxRange nvtx("xr_fill_host");
     if (kind != XR_JUMP && kind != XR_LONG_JUMP) return XR_EINVAL;
     if (S == 0 || m == 0) return XR_OK;
     if (!h_out) return XR_EINVAL;
@@ -748,7 +757,9 @@ extern "C" int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_ba
 // segment start states live in the file-scope device array below instead of
 // context scratch, so the call itself never calls cudaMalloc or cudaFree.
 
-static __device__ __align__(256) unsigned char g_noalloc_segments[XR_NOALLOC_MAX_OUTPUTS >> SEQ_LOG2_NOALLOC][32];
+static __device__ __align__(256) unsigned char g_noalloc_segments[XR_NOALLOC_SCRATCH_BYTES];
+static_assert(((XR_NOALLOC_MAX_OUTPUTS >> SEQ_LOG2_NOALLOC) * 32) == XR_NOALLOC_SCRATCH_BYTES,
+              "the largest call of a 32-byte state fills the array exactly");
 
 // Device address of g_noalloc_segments on each device, looked up once per
 // device (with that device current) by the first call made on it.  In host
@@ -773,21 +784,23 @@ extern "C" int xr_fill_seq_noalloc(xr_ctx *ctx, int variant, void *d_state, size
 {
     if (!ctx || !variant_ok(variant) || !dtype_ok(variant, dtype)) return XR_EINVAL;
     DeviceScope dscope(ctx->device);
-    if (n > (size_t)XR_NOALLOC_MAX_OUTPUTS) return XR_EINVAL;
+    NvtxRange nvtx("xr_fill_seq_noalloc");
+    const size_t sb = (size_t)xr_state_bytes(variant);
+    // P segment states of sb bytes must fit the array: n <= 2^26 for states of
+    // up to 32 bytes, 2^25 for xoshiro512, 2^24 for xoroshiro1024
+    if (n > XR_NOALLOC_MAX_OUTPUTS_FOR(sb)) return XR_EINVAL;
     if (n == 0) return XR_OK;
     const size_t es = (size_t)xr_dtype_bytes(dtype);
     if (!states_ok(d_state) || !d_out || ((uintptr_t)d_out % es)) return XR_EINVAL;
-    {
-        const int erc = ensure_engine(ctx, engine_of(variant));
-        if (erc != XR_OK) return erc;
-    }
+    // the jump tables must exist already: building them would allocate
+    if (!ctx->tables[engine_of(variant)]) return XR_EUNSUPPORTED;
     void *scratch = NULL;
     const int rc = noalloc_scratch(&scratch);
     if (rc != XR_OK) return rc;
     const cudaStream_t st = (cudaStream_t)stream;
     const size_t seg = (size_t)1 << SEQ_LOG2_NOALLOC;
     const size_t full = n / seg, tail = n % seg, P = full + (tail ? 1 : 0);
-    const size_t sb = (size_t)xr_state_bytes(variant);
+    if (P * sb > sizeof(g_noalloc_segments)) return XR_EINVAL;
     // Every slot read below is written first in this call (make_streams fills
     // slots 0 .. P-1: the base copy, then the stream starts), so nothing has
     // to start at zero.

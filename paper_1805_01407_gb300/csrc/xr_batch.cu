@@ -791,6 +791,7 @@ extern "C" int xr_batch_run(xr_batch *b, const uint64_t *d_seeds, void *d_slots,
     if (!b) return XR_EINVAL;
     if (b->plan.reqs.empty()) return XR_OK;
     DeviceScope dscope(b->ctx->device);
+    NvtxRange nvtx("xr_batch_run");
     if (!d_slots || ((uintptr_t)d_slots % 16)) return XR_EINVAL;
     if (b->plan.arena_bytes && (!d_out || ((uintptr_t)d_out % 16))) return XR_EINVAL;
     const cudaStream_t st = (cudaStream_t)stream;
@@ -823,6 +824,7 @@ extern "C" int xr_batch_tune(xr_batch *b, const uint64_t *d_seeds, void *d_slots
 {
     if (!b || !d_slots) return XR_EINVAL;
     DeviceScope dscope(b->ctx->device);
+    NvtxRange nvtx("xr_batch_tune");
     const cudaStream_t st = (cudaStream_t)stream;
     const size_t nbytes = (size_t)(b->plan.max_slot + 1) * 32;
     cudaError_t err = cudaSuccess;

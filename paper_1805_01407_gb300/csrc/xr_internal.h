@@ -8,6 +8,8 @@
 
 #include <atomic>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "xr.h"
 
 namespace xr {
@@ -25,6 +27,9 @@ void count_launch();
 // ones, states of 256 bits or less) have power sets and serve batches.
 constexpr int NUM_ENGINES_H = 7;
 constexpr int NUM_PSET_ENGINES = 5;
+
+// Largest state of any generator (xoroshiro1024: 16 x 64 bits).
+constexpr int XR_MAX_STATE_BYTES = 128;
 
 // Engine of each variant and its state size in bits.
 int engine_of(int variant);
@@ -120,6 +125,16 @@ const uint32_t *dist_sets(xr_ctx *ctx, int engine, int d);
 // The same when already built; otherwise built now unless `st` is capturing
 // (NULL then, and nothing is built).
 const uint32_t *dist_sets_outside_capture(xr_ctx *ctx, int engine, int d, cudaStream_t st);
+// An NVTX range named after the entry point for its duration, so a timeline
+// (Nsight Systems, or ncu's NVTX filters) groups each call's launches.  Costs
+// a branch when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Makes the context's device current for the duration of an entry point and
 // restores the caller's device afterwards (nothing to do when they agree), so
 // calls on contexts of different devices need no cudaSetDevice from the caller.

@@ -304,6 +304,7 @@ static bool complete_finished(xr_server *s)
 
 static cudaError_t launch_round(xr_server *s, Round &R)
 {
+    NvtxRange nvtx("xr_server round");
     // The plan first: admission writes each request's start state straight
     // into its first segment state (seg_base), so the round needs no seed step.
     build_plan(R.reqs.data(), R.reqs.size(), R.plan);
