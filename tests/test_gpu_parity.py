@@ -3,8 +3,11 @@
 Every integer result is compared bit for bit; doubles and floats are compared
 as bit patterns too (the conversions are exact, Sec. 5.3, so the tolerance is
 zero).  Small shapes cover single values, partial tiles and ragged tails;
-the full-size configurations are checked on sampled streams.
+the plain and bulk configurations are compared in full, the 2^24-stream
+jump-start configuration on sampled streams.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -333,34 +336,65 @@ def test_plain_configuration_full(ctx, xr):
             assert_bits_equal(v, (raw >> np.uint64(11)).astype(np.float64) * 2.0**-53)
 
 
+def _host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def compare_streams_in_full(name, kind, base, S, m, d_states, outs, slice_streams=1 << 12):
+    """Every start state and every output of S streams J^i(base), i < S,
+    against the oracle.  The device results are copied back slice by slice
+    (slice_streams streams each) by this thread; the oracle computes the
+    matching slices on every host core (worker threads: the oracle's C calls
+    run without the GIL), one single-threaded oracle per slice.  outs maps a
+    dtype to its device output (S * m elements).  Returns the number of
+    values compared."""
+    from concurrent.futures import ThreadPoolExecutor, wait, FIRST_COMPLETED
+
+    def work(s0, cnt, got_states, got):
+        st = O.streams(name, kind, base, cnt, first=s0)
+        assert (got_states == st).all(), "%s start states %d..%d" % (name, s0, s0 + cnt)
+        raw = O.fill_streams(name, st, m)
+        for dtype, g in got.items():
+            assert_bits_equal(g, expected(name, raw, dtype), "%s %s streams %d..%d" % (name, dtype, s0, s0 + cnt))
+        return cnt * m * len(got)
+
+    cores = _host_cores()
+    done, pending = 0, set()
+    with ThreadPoolExecutor(cores) as ex:
+        for s0 in range(0, S, slice_streams):
+            cnt = min(slice_streams, S - s0)
+            got_states = states_from_device(name, d_states[s0 * len(d_states) // S:(s0 + cnt) * len(d_states) // S])
+            got = {dt: out_to_numpy(o[s0 * m:(s0 + cnt) * m], dt) for dt, o in outs.items()}
+            pending.add(ex.submit(work, s0, cnt, got_states, got))
+            while len(pending) >= 2 * cores:
+                fin, pending = wait(pending, return_when=FIRST_COMPLETED)
+                done += sum(f.result() for f in fin)
+        done += sum(f.result() for f in pending)
+    return done
+
+
 @pytest.mark.parametrize("name", W.BULK_VARIANTS)
-def test_bulk_configuration_sampled(ctx, xr, name):
+def test_bulk_configuration_full(ctx, xr, name):
     """2^20 streams x 2^10 outputs from SplitMix64(42) in the launch
-    configuration the benchmark times; 66 sampled streams compared in full."""
+    configuration the benchmark times (seed, stream starts, tile fill): every
+    start state and every value, as the native word and as doubles (2^31
+    values), against the oracle run on all host cores."""
     import torch
     c = W.CONFIG_BULK
     S, m = c["S"], c["m"]
     base = O.seed(name, c["seed"])
-    d = O.jump_log2(name, c["kind"])
-    idx = W.sample_indices(S, 66, seed=3)
     d_base = ctx.empty_states(name, 1)
     ctx.seed(name, c["seed"], d_base)
     d_states = ctx.empty_states(name, S)
     ctx.make_streams(name, c["kind"], d_base, 0, S, d_states)
-    got_states = states_from_device(name, d_states)
+    outs = {}
     for dtype in (xr.native_dtype(name), "f64"):
-        out = ctx.empty_output(S * m, dtype)
-        ctx.fill(name, d_states, S, m, dtype, out)
-        torch.cuda.synchronize()
-        rows = out.view(S, m)[torch.as_tensor(idx, device="cuda")]
-        got = out_to_numpy(rows.contiguous(), dtype).reshape(len(idx), m)
-        for r, i in enumerate(idx):
-            st = O.jump_pow(name, d, int(i), base)
-            assert (got_states[i] == st).all()
-            raw, _ = O.generate(name, st, m)
-            assert_bits_equal(got[r], expected(name, raw, dtype), "%s %s stream %d" % (name, dtype, i))
-        del out
+        outs[dtype] = ctx.empty_output(S * m, dtype)
+        ctx.fill(name, d_states, S, m, dtype, outs[dtype])
+    torch.cuda.synchronize()
     assert ctx.status() == 0
+    assert compare_streams_in_full(name, c["kind"], base, S, m, d_states, outs) == 2 * S * m
+    del outs
 
 
 @pytest.mark.parametrize("name", ["xoshiro256**", "xoroshiro128+", "xoshiro128++"])
@@ -491,6 +525,22 @@ def test_fill_host_chunks(ctx, xr):
     for i in W.sample_indices(S, 24, seed=5):
         raw, _ = O.generate(name, O.jump_pow(name, d, 7 + int(i), base), m)
         assert_bits_equal(got[i], raw, "stream %d" % i)
+
+
+@pytest.mark.parametrize("name", ["xoshiro512++", "xoroshiro1024**", "xoroshiro64*"])
+def test_fill_host_every_state_size(ctx, xr, name):
+    """The host-buffer call copies the base state into the context before the
+    stream starts: 64- and 128-byte states must arrive whole.  Every stream of
+    a small range (a high first index) is compared with the oracle."""
+    import torch
+    S, m, first = 300, 40, 2**33 + 5
+    base = O.seed(name, 77)
+    dtype = xr.native_dtype(name)
+    h_out = torch.empty(S * m, dtype=xr.torch_dtype(dtype)).pin_memory()
+    ctx.fill_host(name, "long", states_to_bytes(name, base), first, S, m, dtype, h_out)
+    raw = O.bulk_fill(name, "long", base, S, m, first=first).reshape(-1)
+    assert_bits_equal(out_to_numpy(h_out, dtype), expected(name, raw, dtype), name)
+    assert ctx.status() == 0
 
 
 # ------------------------------------------------------------------ errors
