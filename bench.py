@@ -43,7 +43,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["xr", "reference"], default="xr")
-    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -54,7 +54,8 @@ def parse_args():
     p.add_argument("--no-jumpstart", action="store_true")
     p.add_argument("--serve-requests", type=int, default=20000)
     p.add_argument("--batched-steps", type=int, default=5)
-    p.add_argument("--profile", choices=["fill", "streams", "fused", "batch", "lc", "lc-bulk"], default=None,
+    p.add_argument("--profile", choices=["fill", "fill-jobs", "streams", "fused", "batch", "lc", "lc-bulk"],
+                   default=None,
                    help="run a small case for an ncu capture instead of the benchmark")
     p.add_argument("--profile-variant", default="xoshiro256**")
     p.add_argument("--profile-dtype", default=None)
@@ -206,9 +207,91 @@ def recorded_traffic():
         if kv.get("source_sha") != fill_source_hash():
             return None
         return {"bytes_per_launch": float(kv["dram_bytes_per_launch_full_size"]),
-                "algorithmic_bytes_per_launch": float(kv.get("algorithmic_bytes_per_launch", "nan"))}
+                "algorithmic_bytes_per_launch": float(kv.get("algorithmic_bytes_per_launch", "nan")),
+                "note": kv.get("scaling", "")}
     except (OSError, KeyError, ValueError):
         return None
+
+
+def recorded_alu_ops():
+    """ALU-pipe lane operations per value of each fill job, from the committed
+    ncu instruction counts (sm__inst_executed_pipe_alu x 32 / values), if they
+    were taken on the current kernel source; {} otherwise."""
+    path = os.path.join(ROOT, "profiles", "fill_alu_ops__all_generators_2p16x2p10.txt")
+    try:
+        ops, sha = {}, None
+        with open(path) as f:
+            for line in f:
+                if line.startswith("source_sha:"):
+                    sha = line.split(":", 1)[1].strip()
+                parts = line.split()
+                if len(parts) >= 3 and parts[0] in W.ALL_VARIANTS:
+                    ops[(parts[0], parts[1])] = float(parts[2])
+        return ops if sha == fill_source_hash() else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def write_ceiling(xr, out, stream):
+    """The HBM write ceiling measured here: the library's store-only kernel
+    (16-byte stores, 2, 4 or 8 CTAs of 512 threads per SM) and
+    cudaMemsetAsync over the same buffer, best of 10 each, CUDA events on the
+    stream."""
+    import torch
+    nbytes = out.numel() * out.element_size()
+
+    def best(fn, reps=10):
+        fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return nbytes / (min(ts) / 1e3) / 1e9
+
+    store = {k: best(lambda: xr.probe_store(out, k, stream=stream)) for k in (2, 4, 8)}
+    memset = best(lambda: xr.probe_memset(out, stream=stream))
+    peak = max(max(store.values()), memset)
+    return {"write_peak_gbs": peak, "store_kernel_gbs": store, "memset_gbs": memset, "bytes": nbytes,
+            "how": "best of 10, CUDA events on the launching stream, over the bench's 8 GiB output buffer"}
+
+
+def alu_ceiling(xr, stream):
+    """The integer-ALU ceiling measured here: independent lop3 chains on every
+    SM (8 CTAs of 256 threads per SM), lane operations per second, best of 5."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.zeros(4, dtype=torch.int32, device="cuda")
+    blocks, iters = sms * 8, 1 << 16
+    xr.probe_alu(sink, blocks, iters, stream=stream)
+    ts = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        xr.probe_alu(sink, blocks, iters, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    lane_ops = blocks * 256 * iters * 16
+    return {"alu_lane_ops_per_s": lane_ops / (min(ts) / 1e3), "sms": sms, "ms": min(ts),
+            "how": "%d CTAs x 256 threads x %d x 16 lop3, best of 5" % (blocks, iters)}
+
+
+def job_rooflines(jobs_bytes, write_peak, alu_peak, alu_ops):
+    """Per job: the slower of the HBM write bound (write_peak) and the integer
+    bound (alu_peak lane operations/s over the job's ALU operations per
+    value), in GB/s of output, and which binds."""
+    res = {}
+    for (v, d), bpv in jobs_bytes.items():
+        ops = alu_ops.get((v, d))
+        alu_gbs = alu_peak / ops * bpv / 1e9 if ops else None
+        bound = "alu" if alu_gbs is not None and alu_gbs < write_peak else "hbm"
+        res[(v, d)] = {"alu_lane_ops_per_value": ops, "alu_bound_gbs": alu_gbs,
+                       "roofline_gbs": min(write_peak, alu_gbs) if alu_gbs else write_peak, "bound": bound}
+    return res
 
 
 # ---------------------------------------------------------------- oracle timing
@@ -388,16 +471,9 @@ def run_xr(args):
     torch.cuda.synchronize()
     assert ctx.status() == 0
 
-    # store-only reference: cudaMemset of the same 8 GiB buffer
-    t_ms = []
-    for _ in range(5):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        out.zero_()
-        b.record(stream)
-        b.synchronize()
-        t_ms.append(a.elapsed_time(b))
-    memset_gbs = out.numel() / (min(t_ms) / 1e3) / 1e9
+    # the two ceilings of the fill, measured here before the timed region
+    wc = write_ceiling(xr, out, stream)
+    ac = alu_ceiling(xr, stream)
 
     step_events = [new_events() for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -439,6 +515,16 @@ def run_xr(args):
                                      "streams_ms": statistics.median(mk_ms[(v, d)])}
     achieved = fill_bytes / fill_time / 1e9
     traffic = recorded_traffic()
+    alu_ops = recorded_alu_ops()
+    roofs = job_rooflines({(v, d): (S * m * dtype_bytes(d) + S * state_bytes(v)) / (S * m) for v, d in J},
+                          wc["write_peak_gbs"], ac["alu_lane_ops_per_s"], alu_ops)
+    for (v, d), r in roofs.items():
+        pj = per_job["%s/%s" % (v, d)]
+        pj.update(bound=r["bound"], roofline_gbs=r["roofline_gbs"], alu_bound_gbs=r["alu_bound_gbs"],
+                  frac_of_roofline=pj["fill_gbs"] / r["roofline_gbs"])
+    # the step's roofline: every job's bytes at its own bound
+    step_roof = fill_bytes / sum(len(fill_ms[jd]) * (S * m * dtype_bytes(jd[1]) + S * state_bytes(jd[0]))
+                                 / (roofs[jd]["roofline_gbs"] * 1e9) for jd in J) / 1e9
     mk_total = sum(sum(t) for t in mk_ms.values()) / args.steps
     fill_total = sum(sum(t) for t in fill_ms.values()) / args.steps
     line = {
@@ -447,12 +533,20 @@ def run_xr(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": cfg, "impl": "xr",
         "outputs_per_s": world * cfg["values_per_step"] * args.steps / (elapsed_ms / 1e3),
-        "roofline": {"bound": "hbm", "kernel": "k_fill_tma (all 16 jobs)", "achieved": achieved,
+        "roofline": {"bound": "alu" if all(r["bound"] == "alu" for r in roofs.values()) else "hbm",
+                     "kernel": "k_fill_tma (all 16 jobs)", "achieved": achieved,
                      "peak": peak, "peak_kind": "%s hbm_gbs (copy, read+write)" % peak_kind,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic["bytes_per_launch"] if traffic else None,
+                     "traffic_note": traffic["note"] if traffic else None,
                      "algorithmic_bytes_per_launch_u64": S * m * 8 + S * 32,
-                     "memset_gbs": memset_gbs, "frac_of_memset": achieved / memset_gbs},
+                     "write_peak_gbs": wc["write_peak_gbs"], "frac_of_write_peak": achieved / wc["write_peak_gbs"],
+                     "write_ceiling": wc,
+                     "alu_peak_lane_ops_per_s": ac["alu_lane_ops_per_s"], "alu_ceiling": ac,
+                     "jobs_alu_bound": sorted("%s/%s" % jd for jd, r in roofs.items() if r["bound"] == "alu"),
+                     "step_roofline_gbs": step_roof, "frac_of_step_roofline": achieved / step_roof,
+                     "alu_ops_source": "profiles/fill_alu_ops__all_generators_2p16x2p10.txt" if alu_ops
+                     else "not recorded for the current fill source: ALU bound not applied"},
         "step_breakdown_ms": {"fill": fill_total, "make_streams_overlapped": mk_total,
                               "not_in_fills": elapsed_ms / args.steps - fill_total},
         "per_job": per_job,
@@ -467,7 +561,7 @@ def run_xr(args):
     if not args.no_serve:
         line["serving"] = run_serving(xr, ctx, args)
     if not args.no_extra:
-        line["extra_generators"] = run_extra(xr, ctx, args)
+        line["extra_generators"] = run_extra(xr, ctx, args, wc, ac)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             line["extra_generators"]["cpu_baseline"] = extra_cpu_baseline()
     if not args.no_jumpstart:
@@ -534,6 +628,7 @@ def run_batched(xr, ctx, args):
         e1.synchronize()
         plain_ms.append(e0.elapsed_time(e1))
     per_req = sorted(ev[r][0].elapsed_time(ev[r][1]) for r in range(len(specs)))
+    tasks = b.tasks
     b.close()
     q = lambda p: per_req[min(len(per_req) - 1, int(p * len(per_req)))]
     return {
@@ -545,11 +640,11 @@ def run_batched(xr, ctx, args):
         "speedup_vs_plain": plain_ms[-1] / batch_ms,
         "plain_request_ms_p50": q(0.5), "plain_request_ms_p99": q(0.99),
         "tuned": {"outputs_per_row": opt, "block": block, "best_trial_ms": tune_ms},
-        "tasks": b.tasks if False else None,
+        "tasks": tasks,
     }
 
 
-def run_extra(xr, ctx, args):
+def run_extra(xr, ctx, args, wc, ac):
     """The other generators of the paper at the bulk size (2^20 streams x 2^10
     outputs, SplitMix64(42) base, jump-started): fill GB/s per output type,
     median of 5 launches timed with events on their stream."""
@@ -557,6 +652,7 @@ def run_extra(xr, ctx, args):
     S, m, seed = W.CONFIG_BULK["S"], W.CONFIG_BULK["m"], W.CONFIG_BULK["seed"]
     stream = torch.cuda.current_stream()
     peak = measured_peaks()[0]["hbm_gbs"]
+    alu_ops = recorded_alu_ops()
     res = {}
     for v in W.EXTRA_VARIANTS:
         base = ctx.empty_states(v, 1)
@@ -577,7 +673,12 @@ def run_extra(xr, ctx, args):
                 ts.append(a.elapsed_time(b))
             ms = statistics.median(ts)
             gbs = S * m * dtype_bytes(d) / (ms / 1e3) / 1e9
-            res["%s/%s" % (v, d)] = {"fill_gbs": gbs, "fill_ms": ms, "frac_of_measured_peak": gbs / peak}
+            r = job_rooflines({(v, d): dtype_bytes(d)}, wc["write_peak_gbs"], ac["alu_lane_ops_per_s"],
+                              alu_ops)[(v, d)]
+            res["%s/%s" % (v, d)] = {"fill_gbs": gbs, "fill_ms": ms, "frac_of_measured_peak": gbs / peak,
+                                     "bound": r["bound"], "roofline_gbs": r["roofline_gbs"],
+                                     "alu_bound_gbs": r["alu_bound_gbs"],
+                                     "frac_of_roofline": gbs / r["roofline_gbs"]}
             del out
     torch.cuda.synchronize()
     assert ctx.status() == 0
@@ -774,24 +875,31 @@ def run_e2e(ctx, args, first, bytes_per_step, world, dist):
             ctx.fill_host(v, "jump", host_base[v], first, S, m, d, views[d])
 
     step()  # warm-up: staging buffers are allocated on first use
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    link_before = d2h_link_gbs(h_out)
+    times = []
     for _ in range(args.e2e_steps):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         step()
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    el = max_over_ranks(el, dist, "cuda")
+        torch.cuda.synchronize()
+        times.append(max_over_ranks(time.perf_counter() - t0, dist, "cuda"))
+    link_after = d2h_link_gbs(h_out)
     h2d = sum(len(host_base[v]) for v, _ in jobs())
-    value = world * bytes_per_step * args.e2e_steps / el / 1e9
-    link = d2h_link_gbs(h_out)
+    per_step = [world * bytes_per_step / t / 1e9 for t in times]
+    value = statistics.median(per_step)
+    link = statistics.median([link_before, link_after])
     return {"value": value, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": bytes_per_step,
-            "steps": args.e2e_steps, "ms_per_step": 1e3 * el / args.e2e_steps,
+            "steps": args.e2e_steps, "ms_per_step": 1e3 * statistics.median(times),
+            "per_step_gbs": per_step, "spread_gbs": [min(per_step), max(per_step)],
             "api": "xr_fill_host (pinned host output, two staging buffers, copy/compute overlap)",
-            "bound": {"d2h_link_gbs": link, "frac": value / world / link,
-                      "what": "device-to-pinned-host copy bandwidth of this GPU, 1 GiB copies timed with events"}}
+            "bound": {"d2h_link_gbs": link, "d2h_link_before_after_gbs": [link_before, link_after],
+                      "frac": value / world / link, "frac_spread": [min(per_step) / world / link,
+                                                                    max(per_step) / world / link],
+                      "what": "device-to-pinned-host copy bandwidth of this GPU, 1 GiB copies timed with events, "
+                              "before and after the end-to-end steps"}}
 
 
 def d2h_link_gbs(h_out):
@@ -828,6 +936,8 @@ def run_profile(args):
         return run_profile_batch(args)
     if args.profile in ("lc", "lc-bulk"):
         return run_profile_lc(args)
+    if args.profile == "fill-jobs":
+        return run_profile_fill_jobs(args)
     v = args.profile_variant
     d = args.profile_dtype or W.native_dtype(v)
     S, m = args.profile_streams, W.CONFIG_BULK["m"]
@@ -855,6 +965,31 @@ def run_profile(args):
         torch.cuda.synchronize()
         assert ctx.status() == 0
     print("profile case done: %s %s S=%d m=%d" % (args.profile, v, S, m))
+    return 0
+
+
+def run_profile_fill_jobs(args):
+    """One fill launch per generator and output type (every generator x
+    {native word, f64}), --profile-streams streams x 2^10 outputs from
+    SplitMix64(42) jump-started streams, in the order of W.ALL_VARIANTS: for
+    ncu's per-launch instruction counts (ALU operations per value)."""
+    import torch
+    import paper_1805_01407_gb300 as xr
+    S, m = args.profile_streams, W.CONFIG_BULK["m"]
+    with xr.Context(0) as ctx:
+        out = ctx.empty_output(S * m, "u64")
+        order = []
+        for v in W.ALL_VARIANTS:
+            base = ctx.empty_states(v, 1)
+            ctx.seed(v, W.CONFIG_BULK["seed"], base)
+            states = ctx.empty_states(v, S)
+            ctx.make_streams(v, "jump", base, 0, S, states)
+            for d in (W.native_dtype(v), "f64"):
+                ctx.fill(v, states, S, m, d, out.view(xr.torch_dtype(d)))
+                order.append("%s %s" % (v, d))
+        torch.cuda.synchronize()
+        assert ctx.status() == 0
+    print("profile case done: fill launches in order: " + ", ".join(order))
     return 0
 
 

@@ -103,6 +103,9 @@ def lib():
             "xr_fill_host": [vp, i, i, vp, u64, sz, sz, i, vp, vp],
             "xr_status": [vp, i],
             "xr_jump_table": [vp, i, i, vp],
+            "xr_probe_store": [vp, sz, i, vp],
+            "xr_probe_memset": [vp, sz, vp],
+            "xr_probe_alu": [vp, i, i, vp],
         }
         L.xr_launch_count.argtypes = []
         L.xr_launch_count.restype = ctypes.c_uint64
@@ -189,6 +192,25 @@ def jump_log2(variant, kind="jump"):
 def launch_count():
     """Kernels launched through libxr by this process so far."""
     return lib().xr_launch_count()
+
+
+def probe_store(d_buf, ctas_per_sm=0, stream=None):
+    """Store-only kernel over all of d_buf (include/xr_probe.h)."""
+    _need(d_buf, 16, "d_buf")
+    _check(lib().xr_probe_store(d_buf.data_ptr(), _nbytes(d_buf) // 16 * 16, ctas_per_sm, _stream(stream)),
+           "xr_probe_store")
+
+
+def probe_memset(d_buf, stream=None):
+    """cudaMemsetAsync over all of d_buf (include/xr_probe.h)."""
+    _need(d_buf, 1, "d_buf")
+    _check(lib().xr_probe_memset(d_buf.data_ptr(), _nbytes(d_buf), _stream(stream)), "xr_probe_memset")
+
+
+def probe_alu(d_sink, blocks, iters, stream=None):
+    """blocks x 256 threads x iters x 16 lop3 lane operations (include/xr_probe.h)."""
+    _need(d_sink, 4, "d_sink")
+    _check(lib().xr_probe_alu(d_sink.data_ptr(), blocks, iters, _stream(stream)), "xr_probe_alu")
 
 
 def dtype_bytes(dtype):

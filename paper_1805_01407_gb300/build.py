@@ -36,7 +36,8 @@ def sources():
 
 def _deps():
     deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    return deps + [os.path.join(INCLUDE, "xr.h"), os.path.abspath(__file__)]
+    return deps + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")] + \
+        [os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:

@@ -19,8 +19,14 @@ def libxr():
 
 
 def header_functions():
-    text = open(os.path.join(ROOT, "include", "xr.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|uint64_t|const char \*)\s*(xr_\w+)\s*\(", text, re.M)))
+    """Every function declared in include/*.h."""
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            text = open(os.path.join(inc, h)).read()
+            names |= set(re.findall(r"^\s*(?:int|uint64_t|size_t|void \*|const char \*)\s*(xr_\w+)\s*\(", text, re.M))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
