@@ -295,9 +295,12 @@ int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_base, uint64_
 
 /* ---- batching: many uneven requests in one persistent launch ---------------
  * A request asks for the first n outputs of one sequence (as xr_fill_seq),
- * starting from the state in slot `slot` of a caller-owned state table of
- * 32-byte slots (16-byte states use the first half), and writes them at byte
- * offset `out_offset` (a multiple of 16) of a caller-owned output arena.  When
+ * starting from the state in slot `slot` of a caller-owned state table, and
+ * writes them at byte offset `out_offset` (a multiple of 16) of a
+ * caller-owned output arena.  Slots are xr_batch_slot_bytes(b) bytes: 32
+ * when every request's state fits (smaller states use the start of a slot),
+ * 64 when the batch holds xoshiro512 requests and 128 with xoroshiro1024
+ * requests (Sec. 3: 512- and 1024-bit states).  When
  * the batch runs, every request's slot is advanced by its n steps, so the
  * next batch continues each sequence.  Two requests of one batch must not
  * share a slot.  Optionally each slot is first seeded with SplitMix64 from a
@@ -305,10 +308,12 @@ int xr_fill_host(xr_ctx *ctx, int variant, int kind, const void *h_base, uint64_
  *
  * The plan groups requests by (variant, dtype), cuts them into segments of
  * 1024 outputs whose start states come from jump-ahead (power sets, three
- * launches for the whole batch), and packs 32 segments per warp task.  One
- * persistent kernel pulls tasks from a device queue; each lane writes its
- * rows with its own bulk copies, so segments of different requests share a
- * warp.  Results equal xr_fill_seq on each request alone, bit for bit. */
+ * launches for the whole batch; a doubling tree for xoshiro512 and
+ * xoroshiro1024), and packs 32 segments per warp task.  One persistent kernel
+ * pulls tasks from a device queue (a second one serves the 512- and
+ * 1024-bit generators); each lane writes its rows with its own bulk copies,
+ * so segments of different requests share a warp.  Results equal
+ * xr_fill_seq on each request alone, bit for bit. */
 typedef struct {
     int variant;          /* xr_variant */
     int dtype;            /* xr_dtype valid for the variant */
@@ -320,16 +325,20 @@ typedef struct {
 typedef struct xr_batch xr_batch;
 
 /* Plan a batch: checks the requests (XR_EINVAL on a bad variant/dtype, an
- * unaligned offset or a slot used twice), copies the plan to device memory
- * owned by the batch and sizes its scratch.  h_reqs is read during the call
- * only.  The batch keeps using ctx (which must outlive it). */
+ * unaligned offset or a slot used twice), builds the jump tables of the
+ * 512- and 1024-bit engines if a request needs them and the context has
+ * none yet, copies the plan to device memory owned by the batch and sizes
+ * its scratch.  h_reqs is read during the call only.  The batch keeps using
+ * ctx (which must outlive it). */
 int xr_batch_create(xr_ctx *ctx, const xr_request *h_reqs, size_t nreq, xr_batch **out);
 int xr_batch_destroy(xr_batch *b);
 
 /* Bytes of output arena the batch writes (max of out_offset + n * element
- * size over requests), and the number of warp tasks / segments. */
+ * size over requests), the number of warp tasks, and the bytes of one state
+ * slot (32, 64 or 128: the largest state among the requests, at least 32). */
 uint64_t xr_batch_arena_bytes(const xr_batch *b);
 uint64_t xr_batch_tasks(const xr_batch *b);
+uint64_t xr_batch_slot_bytes(const xr_batch *b);
 
 /* Run the batch on `stream`: d_seeds (device, one uint64 per request, or
  * NULL to use the slots as they are), d_slots (device state table), d_out
@@ -353,7 +362,9 @@ int xr_batch_tune(xr_batch *b, const uint64_t *d_seeds, void *d_slots, void *d_o
 
 /* ---- serving: continuous batching for many clients -------------------------
  * A server owns, on the device, one generator state per client (seeded with
- * SplitMix64 from a per-client seed) and an output arena of a fixed budget.
+ * SplitMix64 from a per-client seed; any of the 18 generators, the jump
+ * tables of the 512- and 1024-bit engines built at creation when a client
+ * needs them) and an output arena of a fixed budget.
  * Clients submit requests "the next n outputs of my sequence as dtype" at any
  * time, from any thread.  A scheduler thread admits pending requests in
  * arrival order while arena space (and a round slot) is free; at admission a
@@ -418,7 +429,8 @@ void *xr_server_arena(xr_server *s);
 /* Copy `bytes` of the arena at `offset` to dst (host or device memory, any
  * kind) on `stream` and wait for the copy. */
 int xr_server_read(xr_server *s, uint64_t offset, uint64_t bytes, void *dst, void *stream);
-/* Current state of a client after every admitted request (waits for them). */
+/* Current state of a client after every admitted request (waits for them);
+ * h_words receives the state's bytes (up to 128). */
 int xr_server_client_state(xr_server *s, uint32_t client, void *h_words);
 int xr_server_stats(xr_server *s, xr_serve_stats *out);
 /* Load replay: submit request i at arrival_us[i] microseconds after the call

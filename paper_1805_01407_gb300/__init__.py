@@ -117,6 +117,8 @@ def lib():
         L.xr_batch_arena_bytes.restype = ctypes.c_uint64
         L.xr_batch_tasks.argtypes = [vp]
         L.xr_batch_tasks.restype = ctypes.c_uint64
+        L.xr_batch_slot_bytes.argtypes = [vp]
+        L.xr_batch_slot_bytes.restype = ctypes.c_uint64
         L.xr_batch_run.argtypes = [vp, vp, vp, vp, i, vp]
         L.xr_batch_run.restype = i
         L.xr_batch_set_config.argtypes = [vp, i, i]
@@ -470,10 +472,15 @@ class Batch:
     def tasks(self):
         return lib().xr_batch_tasks(self._h)
 
+    @property
+    def slot_bytes(self):
+        """Bytes per state slot: 32, or 64 / 128 with xoshiro512 / xoroshiro1024 requests."""
+        return lib().xr_batch_slot_bytes(self._h)
+
     def _args(self, d_seeds, d_slots, d_out):
         if d_seeds is not None:
             _need(d_seeds, self.nreq * 8, "d_seeds")
-        _need(d_slots, (self.max_slot + 1) * 32, "d_slots")
+        _need(d_slots, (self.max_slot + 1) * self.slot_bytes, "d_slots")
         if self.arena_bytes:
             _need(d_out, self.arena_bytes, "d_out")
         return (ctypes.c_void_p(d_seeds.data_ptr() if d_seeds is not None else None),
@@ -559,7 +566,7 @@ class Server:
 
     def client_state(self, client):
         nb = state_bytes(self.client_variants[client])
-        buf = ctypes.create_string_buffer(32)
+        buf = ctypes.create_string_buffer(max(nb, 32))
         _check(lib().xr_server_client_state(self._h, client, buf), "xr_server_client_state")
         return buf.raw[:nb]
 

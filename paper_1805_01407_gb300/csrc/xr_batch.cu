@@ -7,7 +7,11 @@
 // Requests with the same (generator, dtype) form a group whose segments are
 // numbered consecutively; a warp task is 32 consecutive segments of a group,
 // so small requests share warps without divergent code paths.  One persistent
-// kernel pulls tasks from a device counter.  Each lane stages its rows in its
+// kernel pulls tasks from a device counter.  The generators with 64- and
+// 128-byte states (xoshiro512, xoroshiro1024) have no power sets: their
+// segment starts come from a doubling tree batched over their requests, and
+// their tasks run in a second instance of the persistent kernel, so the
+// kernel of the other generators keeps its registers.  Each lane stages its rows in its
 // own shared-memory buffers and writes them with its own bulk copies
 // (cp.async.bulk), so lanes of different requests never wait for each other.
 #include <algorithm>
@@ -26,7 +30,6 @@ namespace xr {
 constexpr int BSEG_LOG2 = 10;            // outputs per segment = 1024
 constexpr u64 BSEG = 1ull << BSEG_LOG2;
 constexpr int BATCH_NBUF = 2;            // staged rows per lane
-constexpr int SLOT_WORDS = 8;            // 32-byte state slots
 constexpr int TILE_BYTES_B = 32 * 128;   // one 32-row x 128-byte tile
 
 struct BatchDev {
@@ -39,6 +42,7 @@ struct BatchDev {
     unsigned long long *counter;
     u32 *segstates;
     unsigned char *slots;
+    u32 sw;             // 32-bit words per state slot and per segment state (8, 16 or 32)
     unsigned char *out;
     const u64 *seeds;
     int *status;
@@ -52,46 +56,48 @@ constexpr u64 TASK_FULL = 1ull << 63;  // 32 full segments of one row-aligned re
 
 // ---------------------------------------------------------------- seeding / copy-in
 
+// State bytes of a generator (the order of enum xr_variant).
+__device__ __forceinline__ int batch_state_bytes(int v)
+{
+    return v <= 2 ? 32 : v <= 9 ? 16 : v <= 11 ? 8 : v <= 14 ? 64 : 128;
+}
+
 // Slot state (or SplitMix64 of the request's seed, also written to the slot)
-// becomes segment 0 of the request.
+// becomes segment 0 of the request.  Slots and segment states are d.sw words;
+// the words past the state are written as zero.
 __global__ void k_batch_seed(BatchDev d, size_t nreq)
 {
     const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nreq) return;
     const BReq q = d.reqs[r];
-    u32 w[SLOT_WORDS];
-    u32 *slot = reinterpret_cast<u32 *>(d.slots + q.slot * 32);
-    // 64-bit SplitMix64 outputs per state: 32-byte states take 4, 16-byte 2,
-    // 8-byte 1 (32-bit words take each output's low half first, so the u32
-    // words come out in the same order either way).
-    const int outs = q.variant <= 2 ? 4 : (q.variant <= 9 ? 2 : 1);
-    if (d.seeds) {
-        u64 x = d.seeds[r];
-#pragma unroll
-        for (int j = 0; j < SLOT_WORDS; ++j) w[j] = 0u;
-        for (int j = 0; j < outs; ++j) {
-            const u64 z = splitmix64_next(x);
-            w[2 * j] = (u32)z;
-            w[2 * j + 1] = (u32)(z >> 32);
-        }
-        reinterpret_cast<uint4 *>(slot)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        reinterpret_cast<uint4 *>(slot)[1] = make_uint4(w[4], w[5], w[6], w[7]);
-    } else {
-        const uint4 a = reinterpret_cast<const uint4 *>(slot)[0];
-        const uint4 b = reinterpret_cast<const uint4 *>(slot)[1];
-        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-        w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
-        for (int j = 2 * outs; j < SLOT_WORDS; ++j) w[j] = 0u;
-    }
+    uint4 *slot = reinterpret_cast<uint4 *>(d.slots + q.slot * (u64)d.sw * 4u);
+    uint4 *dst = q.n > 0 ? reinterpret_cast<uint4 *>(d.segstates + q.seg_base * (u64)d.sw) : nullptr;
+    // 64-bit SplitMix64 outputs per state: one per 8 state bytes (32-bit words
+    // take each output's low half first, so the u32 words come out in the same
+    // order either way)
+    const int sb = batch_state_bytes(q.variant), outs = (sb + 7) / 8;
+    u64 x = d.seeds ? d.seeds[r] : 0ull;
     u32 any = 0;
+    for (u32 k = 0; k < d.sw / 4; ++k) {  // 16 bytes = two SplitMix64 outputs at a time
+        u32 w[4];
+        if (d.seeds) {
 #pragma unroll
-    for (int j = 0; j < SLOT_WORDS; ++j) any |= w[j];
-    if (!any) atomicCAS(d.status, 0, XR_EZERO_STATE);
-    if (q.n > 0) {
-        uint4 *dst = reinterpret_cast<uint4 *>(d.segstates + q.seg_base * SLOT_WORDS);
-        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+            for (int h = 0; h < 2; ++h) {
+                const bool used = (int)(2 * k + h) < outs;
+                const u64 z = used ? splitmix64_next(x) : 0ull;
+                w[2 * h] = (u32)z;
+                w[2 * h + 1] = (u32)(z >> 32);
+            }
+            slot[k] = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            const uint4 a = (int)(16 * k) < sb ? slot[k] : make_uint4(0u, 0u, 0u, 0u);
+            w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+            if ((int)(16 * k + 8) >= sb) w[2] = w[3] = 0u;  // an 8-byte state in a 16-byte piece
+        }
+        any |= w[0] | w[1] | w[2] | w[3];
+        if (dst) dst[k] = make_uint4(w[0], w[1], w[2], w[3]);
     }
+    if (!any) atomicCAS(d.status, 0, XR_EZERO_STATE);
 }
 
 // ---------------------------------------------------------------- segment starts
@@ -117,12 +123,13 @@ struct LevelEngine {
 struct LevelArgs {
     LevelEngine e[NUM_PSET_ENGINES];
     int n;
+    u32 sw;  // words per segment state
     u64 stride;
 };
 
 template <int NW>
-__device__ __forceinline__ void batch_level_cta(const LevelEngine &E, unsigned x, int j, u64 stride, u32 *segstates,
-                                                u32 *T)
+__device__ __forceinline__ void batch_level_cta(const LevelEngine &E, unsigned x, int j, u64 stride, u32 sw,
+                                                u32 *segstates, u32 *T)
 {
     typedef Russians<NW> RT;
     {
@@ -138,10 +145,10 @@ __device__ __forceinline__ void batch_level_cta(const LevelEngine &E, unsigned x
         const BLevelItem it = E.items[idx];
         const u64 child = it.parent + (u64)j * stride;
         if (child >= it.limit) continue;
-        // 32-byte slots: whole 16-byte loads and stores (the unused words of a
-        // slot are written as zero)
+        // whole 16-byte loads and stores of the first 32 bytes of a segment
+        // state (the unused words among them are written as zero)
         u32 v[NW], r[NW];
-        const uint4 *ps = reinterpret_cast<const uint4 *>(segstates + it.parent * SLOT_WORDS);
+        const uint4 *ps = reinterpret_cast<const uint4 *>(segstates + it.parent * sw);
         const uint4 a = ps[0];
         v[0] = a.x; v[1] = a.y;
         if constexpr (NW >= 4) { v[2] = a.z; v[3] = a.w; }
@@ -150,7 +157,7 @@ __device__ __forceinline__ void batch_level_cta(const LevelEngine &E, unsigned x
             v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
         }
         russians_matvec<NW>(T, v, r);
-        uint4 *cs = reinterpret_cast<uint4 *>(segstates + child * SLOT_WORDS);
+        uint4 *cs = reinterpret_cast<uint4 *>(segstates + child * sw);
         if constexpr (NW == 8) {
             cs[0] = make_uint4(r[0], r[1], r[2], r[3]);
             cs[1] = make_uint4(r[4], r[5], r[6], r[7]);
@@ -173,9 +180,34 @@ __global__ void __launch_bounds__(BLEVEL_THREADS) k_batch_level(const LevelArgs 
     const int j = blockIdx.y + 1;
     if ((unsigned)j > E.maxj) return;
     const unsigned x = blockIdx.x - E.cta_first;
-    if (E.nw == 8) batch_level_cta<8>(E, x, j, a.stride, segstates, T);
-    else if (E.nw == 4) batch_level_cta<4>(E, x, j, a.stride, segstates, T);
-    else batch_level_cta<2>(E, x, j, a.stride, segstates, T);
+    if (E.nw == 8) batch_level_cta<8>(E, x, j, a.stride, a.sw, segstates, T);
+    else if (E.nw == 4) batch_level_cta<4>(E, x, j, a.stride, a.sw, segstates, T);
+    else batch_level_cta<2>(E, x, j, a.stride, a.sw, segstates, T);
+}
+
+// One level of the doubling tree of the engines without power sets: product
+// t of the launch belongs to the item k with prefix[k] <= t < prefix[k + 1];
+// segment seg_base + half + i = M (segment seg_base + i), i = t - prefix[k].
+// M = T^(2^(10 + L)) is read through the read-only cache by every thread in
+// the same order (warp-uniform loads).
+template <int NW>
+__global__ void __launch_bounds__(128)
+    k_batch_tree(const u32 *__restrict__ M, const BTreeItem *items, u32 nitems, u64 work, u64 half, u32 sw,
+                 u32 *segstates)
+{
+    const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= work) return;
+    u32 lo = 0, hi = nitems;  // prefix[lo] <= t < prefix[hi] (prefix[nitems] = work)
+    while (hi - lo > 1) {
+        const u32 mid = (lo + hi) >> 1;
+        if (items[mid].prefix <= t) lo = mid;
+        else hi = mid;
+    }
+    const u64 parent = items[lo].seg_base + (t - items[lo].prefix);
+    u32 v[NW], r[NW];
+    load_vec<NW>(v, segstates + parent * sw);
+    f2_matvec<NW, false>(M, v, r);
+    store_vec<NW>(r, segstates + (parent + half) * sw);
 }
 
 // ---------------------------------------------------------------- persistent fill
@@ -305,6 +337,9 @@ __device__ __forceinline__ void batch_warp_rows(const u32 *st, unsigned char *sl
         else batch_lane<V, DT>(st, slot, out, count, buf0, bufnext, d.opt);               \
         break;
 
+// LARGE = false: the generators with states of up to 32 bytes (0 .. 11);
+// LARGE = true: xoshiro512 and xoroshiro1024 (12 .. 17).
+template <bool LARGE>
 __global__ void __launch_bounds__(512)
     k_batch_fill(BatchDev d, const __grid_constant__ CUtensorMap map64, const __grid_constant__ CUtensorMap map32)
 {
@@ -337,11 +372,24 @@ __global__ void __launch_bounds__(512)
         const u64 seg = s - pre[lo];
         const u64 start = seg << BSEG_LOG2;
         const u64 count = (q.n - start) < BSEG ? (q.n - start) : BSEG;
-        const u32 *st = d.segstates + (q.seg_base + seg) * SLOT_WORDS;
-        unsigned char *slot = (start + count == q.n) ? d.slots + q.slot * 32 : nullptr;
+        const u32 *st = d.segstates + (q.seg_base + seg) * (u64)d.sw;
+        unsigned char *slot = (start + count == q.n) ? d.slots + q.slot * (u64)d.sw * 4u : nullptr;
         const int es = (g.dtype == DT_U64 || g.dtype == DT_F64) ? 8 : 4;
         unsigned char *out = d.out + q.out_offset + start * (u64)es;
         const int row0 = (int)(q.out_offset / (BSEG * (u64)es) + seg - (u64)lane);
+        if constexpr (LARGE) {
+            switch (g.variant * 4 + g.dtype) {
+                XR_BATCH_CASE(12, DT_U64) XR_BATCH_CASE(12, DT_F64) XR_BATCH_CASE(12, DT_F32)
+                XR_BATCH_CASE(13, DT_U64) XR_BATCH_CASE(13, DT_F64) XR_BATCH_CASE(13, DT_F32)
+                XR_BATCH_CASE(14, DT_U64) XR_BATCH_CASE(14, DT_F64) XR_BATCH_CASE(14, DT_F32)
+                XR_BATCH_CASE(15, DT_U64) XR_BATCH_CASE(15, DT_F64) XR_BATCH_CASE(15, DT_F32)
+                XR_BATCH_CASE(16, DT_U64) XR_BATCH_CASE(16, DT_F64) XR_BATCH_CASE(16, DT_F32)
+                XR_BATCH_CASE(17, DT_U64) XR_BATCH_CASE(17, DT_F64) XR_BATCH_CASE(17, DT_F32)
+            default:
+                break;
+            }
+            continue;
+        }
         switch (g.variant * 4 + g.dtype) {
             XR_BATCH_CASE(0, DT_U64) XR_BATCH_CASE(0, DT_F64) XR_BATCH_CASE(0, DT_F32)
             XR_BATCH_CASE(1, DT_U64) XR_BATCH_CASE(1, DT_F64) XR_BATCH_CASE(1, DT_F32)
@@ -381,6 +429,12 @@ static bool dtype_ok_b(int v, int dt)
     return false;
 }
 
+unsigned int slot_words_of(int variant)
+{
+    const int b = xr_state_bytes(variant);
+    return b <= 32 ? 8u : (unsigned)b / 4u;
+}
+
 int check_requests(const xr_request *h, size_t nreq)
 {
     std::vector<u64> slots;
@@ -388,7 +442,6 @@ int check_requests(const xr_request *h, size_t nreq)
     for (size_t r = 0; r < nreq; ++r) {
         const xr_request &q = h[r];
         if (q.variant < 0 || q.variant >= XR_NUM_VARIANTS || !dtype_ok_b(q.variant, q.dtype)) return XR_EINVAL;
-        if (engine_of(q.variant) >= NUM_PSET_ENGINES) return XR_EUNSUPPORTED;  // states over 32 bytes
         if (q.out_offset % 16) return XR_EINVAL;
         if (q.n > (1ull << 50)) return XR_EINVAL;
         slots.push_back(q.slot);
@@ -411,6 +464,9 @@ void build_plan(const xr_request *in, size_t nreq, HostPlan &p)
     p.tasks.clear();
     p.items.clear();
     p.levels.clear();
+    p.titems.clear();
+    p.trees.clear();
+    p.slot_words = 8;
     u64 segs = 0, arena = 0, maxslot = 0;
     for (size_t r = 0; r < nreq; ++r) {
         BReq &q = p.reqs[r];
@@ -423,6 +479,7 @@ void build_plan(const xr_request *in, size_t nreq, HostPlan &p)
         segs += (q.n + BSEG - 1) / BSEG;
         arena = std::max<u64>(arena, q.out_offset + q.n * (u64)es_of(q.dtype));
         maxslot = std::max<u64>(maxslot, q.slot);
+        p.slot_words = std::max(p.slot_words, slot_words_of(q.variant));
     }
     p.nseg = segs;
     p.arena_bytes = arena;
@@ -431,9 +488,12 @@ void build_plan(const xr_request *in, size_t nreq, HostPlan &p)
     std::vector<u32> bucket[XR_NUM_VARIANTS * 4];
     for (size_t r = 0; r < nreq; ++r)
         if (p.reqs[r].n) bucket[p.reqs[r].variant * 4 + p.reqs[r].dtype].push_back((u32)r);
-    std::vector<u64> partial[BSEG + 1];  // partial tasks by longest lane
+    // partial tasks by longest lane; [1] for the large generators
+    std::vector<u64> partial[2][BSEG + 1];
+    std::vector<u64> full_tasks[2];
     for (int bi = 0; bi < XR_NUM_VARIANTS * 4; ++bi) {
         if (bucket[bi].empty()) continue;
+        const int big = engine_of(bi / 4) >= NUM_PSET_ENGINES ? 1 : 0;
         BGroup g;
         g.variant = bi / 4;
         g.dtype = bi % 4;
@@ -469,12 +529,16 @@ void build_plan(const xr_request *in, size_t nreq, HostPlan &p)
             pre += P;
         }
         for (u64 t = 0; t < T; ++t) {
-            if (full[t]) p.tasks.push_back((gi << 40) | t | TASK_FULL);
-            else partial[len[t]].push_back((gi << 40) | t);
+            if (full[t]) full_tasks[big].push_back((gi << 40) | t | TASK_FULL);
+            else partial[big][len[t]].push_back((gi << 40) | t);
         }
     }
-    for (int l = (int)BSEG; l >= 0; --l)
-        p.tasks.insert(p.tasks.end(), partial[l].begin(), partial[l].end());
+    for (int big = 0; big < 2; ++big) {
+        p.tasks.insert(p.tasks.end(), full_tasks[big].begin(), full_tasks[big].end());
+        for (int l = (int)BSEG; l >= 0; --l)
+            p.tasks.insert(p.tasks.end(), partial[big][l].begin(), partial[big][l].end());
+        if (big == 0) p.ntasks_small = p.tasks.size();
+    }
 
     // levels of the segment-start scheme, per (level, engine)
     for (int l = PSET_LEVELS - 1; l >= 0; --l) {
@@ -499,6 +563,28 @@ void build_plan(const xr_request *in, size_t nreq, HostPlan &p)
             const u64 kids = (p.items[L.first].limit - p.items[L.first].parent + stride - 1) / stride;
             L.maxj = (unsigned)std::min<u64>(kids - 1, PSET_SIZE - 1);
             p.levels.push_back(L);
+        }
+    }
+    // doubling-tree levels of the engines without power sets
+    for (int e = NUM_PSET_ENGINES; e < NUM_ENGINES_H; ++e) {
+        for (int L = 0; L < 64; ++L) {
+            const u64 half = 1ull << L;
+            TreeLaunch t;
+            t.engine = e;
+            t.level = L;
+            t.first = p.titems.size();
+            u64 work = 0;
+            for (size_t r = 0; r < nreq; ++r) {
+                if (engine_of(p.reqs[r].variant) != e) continue;
+                const u64 P = (p.reqs[r].n + BSEG - 1) / BSEG;
+                if (P <= half) continue;
+                p.titems.push_back({p.reqs[r].seg_base, work});
+                work += std::min<u64>(half, P - half);
+            }
+            t.count = p.titems.size() - t.first;
+            t.work = work;
+            if (!t.count) break;
+            p.trees.push_back(t);
         }
     }
 }
@@ -526,7 +612,8 @@ cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st, const vo
     d.off_prefix = up256(d.off_group_reqs + p.group_reqs.size() * sizeof(u32));
     d.off_tasks = up256(d.off_prefix + p.prefix.size() * sizeof(u64));
     d.off_items = up256(d.off_tasks + p.tasks.size() * sizeof(u64));
-    d.off_extra = up256(d.off_items + p.items.size() * sizeof(BLevelItem));
+    d.off_titems = up256(d.off_items + p.items.size() * sizeof(BLevelItem));
+    d.off_extra = up256(d.off_titems + p.titems.size() * sizeof(BTreeItem));
     d.off_counter = up256(d.off_extra + extra_bytes);
     const size_t total = d.off_counter + 256;
     cudaError_t err = cudaSuccess;
@@ -542,7 +629,7 @@ cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st, const vo
         if (err != cudaSuccess) return err;
         d.blob_cap = cap;
     }
-    const size_t segbytes = (size_t)p.nseg * 32;
+    const size_t segbytes = (size_t)p.nseg * p.slot_words * 4;
     if (segbytes > d.seg_cap) {
         err = cudaStreamSynchronize(st);
         cudaFree(d.segstates);
@@ -552,8 +639,8 @@ cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st, const vo
         if (err != cudaSuccess) return err;
         d.seg_cap = segbytes;
     }
-    if (!d.counter) {
-        err = cudaMalloc((void **)&d.counter, sizeof(unsigned long long));
+    if (!d.counter) {  // two task counters: the small and the large generators
+        err = cudaMalloc((void **)&d.counter, 2 * sizeof(unsigned long long));
         if (err != cudaSuccess) return err;
     }
     auto put = [&](size_t off, const void *src, size_t bytes) {
@@ -565,8 +652,9 @@ cudaError_t upload_plan(const HostPlan &p, DevPlan &d, cudaStream_t st, const vo
     put(d.off_prefix, p.prefix.data(), p.prefix.size() * sizeof(u64));
     put(d.off_tasks, p.tasks.data(), p.tasks.size() * sizeof(u64));
     put(d.off_items, p.items.data(), p.items.size() * sizeof(BLevelItem));
+    put(d.off_titems, p.titems.data(), p.titems.size() * sizeof(BTreeItem));
     put(d.off_extra, extra, extra_bytes);
-    memset(d.pinned + d.off_counter, 0, sizeof(unsigned long long));
+    memset(d.pinned + d.off_counter, 0, 2 * sizeof(unsigned long long));
     return cudaMemcpyAsync(d.blob, d.pinned, total, cudaMemcpyHostToDevice, st);
 }
 
@@ -596,9 +684,11 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
     d.prefix = (const u64 *)(dp.blob + dp.off_prefix);
     d.tasks = (const u64 *)(dp.blob + dp.off_tasks);
     const BLevelItem *items = (const BLevelItem *)(dp.blob + dp.off_items);
-    d.ntasks = p.tasks.size();
+    const BTreeItem *titems = (const BTreeItem *)(dp.blob + dp.off_titems);
+    d.ntasks = p.ntasks_small;
     d.counter = round_ready ? reinterpret_cast<unsigned long long *>(dp.blob + dp.off_counter) : dp.counter;
     d.segstates = dp.segstates;
+    d.sw = p.slot_words;
     d.slots = (unsigned char *)d_slots;
     d.out = (unsigned char *)d_out;
     d.seeds = reinterpret_cast<const u64 *>(d_seeds);
@@ -639,7 +729,7 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
     if (nreq == 0) return cudaSuccess;
     cudaError_t err = cudaSuccess;
     if (!round_ready) {
-        err = cudaMemsetAsync(dp.counter, 0, sizeof(unsigned long long), st);
+        err = cudaMemsetAsync(dp.counter, 0, 2 * sizeof(unsigned long long), st);
         if (err != cudaSuccess) return err;
         k_batch_seed<<<(unsigned)((nreq + 127) / 128), 128, 0, st>>>(d, nreq);
         count_launch();
@@ -650,6 +740,7 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
     for (size_t i = 0; i < p.levels.size() && err == cudaSuccess;) {
         LevelArgs a;
         a.n = 0;
+        a.sw = p.slot_words;
         a.stride = 1ull << (PSET_BITS * p.levels[i].level);
         unsigned ctas = 0, maxj = 0;
         const size_t per_cta = (size_t)BLEVEL_THREADS * BLEVEL_ITEMS_PER_THREAD;
@@ -672,28 +763,55 @@ cudaError_t enqueue_plan(xr_ctx *ctx, const HostPlan &p, DevPlan &dp, const uint
         count_launch();
         err = cudaGetLastError();
     }
-    if (err != cudaSuccess || p.tasks.empty()) return err;
-    static std::atomic<uint64_t> attr{0};
-    err = set_smem_once(attr, k_batch_fill, 227 * 1024);
-    if (err != cudaSuccess) return err;
-    const size_t smem = batch_smem_bytes(opt, block);
-    if (dp.occ_opt != opt || dp.occ_block != block) {  // occupancy per configuration, once
-        int per_sm = 0, sms = 0;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_fill, block, smem);
-        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-        if (err != cudaSuccess) return err;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        dp.occ_opt = opt;
-        dp.occ_block = block;
-        dp.occ_per_sm = per_sm;
-        dp.occ_sms = sms;
+    // doubling-tree levels of xoshiro512 / xoroshiro1024 (in level order)
+    for (size_t i = 0; i < p.trees.size() && err == cudaSuccess; ++i) {
+        const TreeLaunch &L = p.trees[i];
+        const int n = engine_bits(L.engine);
+        const u32 *M = ctx->tables[L.engine] + (size_t)((BSEG_LOG2 + L.level) % n) * n * (n / 32);
+        const unsigned grid = (unsigned)((L.work + 127) / 128);
+        if (n == 512)
+            k_batch_tree<16><<<grid, 128, 0, st>>>(M, titems + L.first, (u32)L.count, L.work, 1ull << L.level,
+                                                   p.slot_words, dp.segstates);
+        else
+            k_batch_tree<32><<<grid, 128, 0, st>>>(M, titems + L.first, (u32)L.count, L.work, 1ull << L.level,
+                                                   p.slot_words, dp.segstates);
+        count_launch();
+        err = cudaGetLastError();
     }
+    if (err != cudaSuccess || p.tasks.empty()) return err;
+    const size_t smem = batch_smem_bytes(opt, block);
     const u64 warps_per_block = (u64)block / 32;
-    const u64 grid = std::min<u64>((u64)dp.occ_per_sm * dp.occ_sms,
-                                   (p.tasks.size() + warps_per_block - 1) / warps_per_block);
-    k_batch_fill<<<(unsigned)grid, block, smem, st>>>(d, dp.maps[0], dp.maps[1]);
-    count_launch();
-    return cudaGetLastError();
+    // the persistent fill of the small generators, then of the large ones
+    for (int big = 0; big < 2 && err == cudaSuccess; ++big) {
+        const u64 first = big ? p.ntasks_small : 0, ntasks = big ? p.tasks.size() - p.ntasks_small : p.ntasks_small;
+        if (!ntasks) continue;
+        BatchDev db = d;
+        db.tasks = d.tasks + first;
+        db.ntasks = ntasks;
+        db.counter = d.counter + big;
+        auto kern = big ? k_batch_fill<true> : k_batch_fill<false>;
+        static std::atomic<uint64_t> attr[2];
+        err = set_smem_once(attr[big], kern, 227 * 1024);
+        if (err != cudaSuccess) return err;
+        int &occ_opt = big ? dp.occ_large_opt : dp.occ_opt, &occ_block = big ? dp.occ_large_block : dp.occ_block;
+        int &occ_per_sm = big ? dp.occ_large_per_sm : dp.occ_per_sm;
+        if (occ_opt != opt || occ_block != block) {  // occupancy per configuration, once
+            int per_sm = 0, sms = 0;
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+            if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+            if (err != cudaSuccess) return err;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            occ_opt = opt;
+            occ_block = block;
+            occ_per_sm = per_sm;
+            dp.occ_sms = sms;
+        }
+        const u64 grid = std::min<u64>((u64)occ_per_sm * dp.occ_sms, (ntasks + warps_per_block - 1) / warps_per_block);
+        kern<<<(unsigned)grid, block, smem, st>>>(db, dp.maps[0], dp.maps[1]);
+        count_launch();
+        err = cudaGetLastError();
+    }
+    return err;
 }
 
 }  // namespace xr
@@ -743,10 +861,14 @@ extern "C" int xr_batch_create(xr_ctx *ctx, const xr_request *h_reqs, size_t nre
     *out = nullptr;
     const int rc = check_requests(h_reqs, nreq);
     if (rc != XR_OK) return rc;
+    DeviceScope dscope(ctx->device);
+    for (size_t r = 0; r < nreq; ++r) {  // the large engines' tables are built on first use
+        const int erc = ensure_engine(ctx, engine_of(h_reqs[r].variant));
+        if (erc != XR_OK) return erc;
+    }
     xr_batch *b = new xr_batch();
     b->ctx = ctx;
     build_plan(h_reqs, nreq, b->plan);
-    DeviceScope dscope(ctx->device);
     cudaError_t err = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (err == cudaSuccess) err = upload_plan(b->plan, b->dev, b->cap);
     if (err == cudaSuccess) err = cudaStreamSynchronize(b->cap);
@@ -760,6 +882,7 @@ extern "C" int xr_batch_create(xr_ctx *ctx, const xr_request *h_reqs, size_t nre
 
 extern "C" uint64_t xr_batch_arena_bytes(const xr_batch *b) { return b ? b->plan.arena_bytes : 0; }
 extern "C" uint64_t xr_batch_tasks(const xr_batch *b) { return b ? (uint64_t)b->plan.tasks.size() : 0; }
+extern "C" uint64_t xr_batch_slot_bytes(const xr_batch *b) { return b ? (uint64_t)b->plan.slot_words * 4u : 0; }
 
 extern "C" int xr_batch_set_config(xr_batch *b, int opt, int block)
 {
@@ -826,7 +949,7 @@ extern "C" int xr_batch_tune(xr_batch *b, const uint64_t *d_seeds, void *d_slots
     DeviceScope dscope(b->ctx->device);
     NvtxRange nvtx("xr_batch_tune");
     const cudaStream_t st = (cudaStream_t)stream;
-    const size_t nbytes = (size_t)(b->plan.max_slot + 1) * 32;
+    const size_t nbytes = (size_t)(b->plan.max_slot + 1) * b->plan.slot_words * 4;
     cudaError_t err = cudaSuccess;
     if (b->slot_backup_bytes < nbytes) {
         cudaFree(b->d_slot_backup);

@@ -9,6 +9,36 @@
 
 namespace xr {
 
+// ---------------------------------------------------------------- vectors
+// A state as NW u32 words, moved with 16-byte (8-byte for NW = 2) accesses.
+
+template <int NW>
+__device__ __forceinline__ void load_vec(u32 (&v)[NW], const u32 *p)
+{
+    if constexpr (NW >= 4) {
+#pragma unroll
+        for (int q = 0; q < NW / 4; ++q) {
+            const uint4 a = reinterpret_cast<const uint4 *>(p)[q];
+            v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+        }
+    } else {
+        const uint2 a = reinterpret_cast<const uint2 *>(p)[0];
+        v[0] = a.x; v[1] = a.y;
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void store_vec(const u32 (&v)[NW], u32 *p)
+{
+    if constexpr (NW >= 4) {
+#pragma unroll
+        for (int q = 0; q < NW / 4; ++q)
+            reinterpret_cast<uint4 *>(p)[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+        reinterpret_cast<uint2 *>(p)[0] = make_uint2(v[0], v[1]);
+    }
+}
+
 // ---------------------------------------------------------------- F2 algebra
 // A state is a column vector of n bits; bit c is bit c % 32 of u32 word c / 32
 // of the state in memory.  A matrix is stored by columns: column c (the image

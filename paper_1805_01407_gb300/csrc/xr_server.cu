@@ -35,49 +35,69 @@ struct AdmitClient {
 struct AdmitReq {
     u64 n, slot;
 };
+// Jump tables of every engine (T^(2^k)), and the single-step power sets of
+// the engines that have them (null for xoshiro512 and xoroshiro1024).
 struct Tables4 {
-    const u32 *t[NUM_PSET_ENGINES];
+    const u32 *t[NUM_ENGINES_H];
 };
 
-// State words of a client slot (32 bytes) <- SplitMix64(seed), by engine.
-__global__ void k_server_seed(const int *variants, const u64 *seeds, u32 nclients, u32 *cstates)
+// Client state slots of sw words <- SplitMix64(seed): one 64-bit output per 8
+// state bytes (32-bit words take each output's low half first); words past
+// the state are zero.
+__global__ void k_server_seed(const int *variants, const u64 *seeds, u32 nclients, u32 sw, u32 *cstates)
 {
     const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nclients) return;
     u64 x = seeds[c];
-    u32 w[8];
+    const int v = variants[c];
+    const int sb = v <= 2 ? 32 : v <= 9 ? 16 : v <= 11 ? 8 : v <= 14 ? 64 : 128;
+    uint4 *d = reinterpret_cast<uint4 *>(cstates + (size_t)c * sw);
+    for (u32 k = 0; k < sw / 4; ++k) {
+        u32 w[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) w[j] = 0u;
-    const int words64 = variants[c] <= 2 ? 4 : (variants[c] <= 9 ? 2 : 1);
-    for (int j = 0; j < words64; ++j) {
-        const u64 z = splitmix64_next(x);
-        w[2 * j] = (u32)z;
-        w[2 * j + 1] = (u32)(z >> 32);
+        for (int h = 0; h < 2; ++h) {
+            const u64 z = (int)(16 * k + 8 * h) < sb ? splitmix64_next(x) : 0ull;
+            w[2 * h] = (u32)z;
+            w[2 * h + 1] = (u32)(z >> 32);
+        }
+        d[k] = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    uint4 *d = reinterpret_cast<uint4 *>(cstates + (size_t)c * 8);
-    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// v <- T^e v by one warp from the jump tables alone (one product per set bit
+// of e), for the engines without power sets.
+template <int NW>
+__device__ void warp_advance_tables(const u32 *tables, u32 (&v)[NW], u64 e, int lane)
+{
+    constexpr int n = NW * 32;
+    while (e) {
+        const int k = __ffsll((long long)e) - 1;
+        e &= e - 1;
+        warp_matvec<NW>(tables + (size_t)k * n * NW, v, lane);
+    }
 }
 
 // One client's admitted requests in order, by one warp: each request gets the
-// current state in its 32-byte destination (req.slot indexes `rslots`: a
+// current state in its destination of sw words (req.slot indexes `rslots`: a
 // round's segment states, at the request's first segment, or a plain slot),
 // then the state advances by the request's n.
 template <int NW>
 __device__ void admit_chain(const u32 *psets0, const u32 *tables, u32 *cstate, const AdmitReq *reqs, u32 first,
-                            u32 count, unsigned char *rslots, int lane)
+                            u32 count, unsigned char *rslots, u32 sw, int lane)
 {
+    constexpr int W = NW < 8 ? 8 : NW;  // words written: the state, zero-padded to 32 bytes
     u32 v[NW];
 #pragma unroll
     for (int j = 0; j < NW; ++j) v[j] = cstate[j];
     for (u32 i = 0; i < count; ++i) {
         const AdmitReq q = reqs[first + i];
         if (lane == 0) {
-            u32 *d = reinterpret_cast<u32 *>(rslots + q.slot * 32);
+            u32 *d = reinterpret_cast<u32 *>(rslots + q.slot * sw * 4u);
 #pragma unroll
-            for (int w = 0; w < 8; ++w) d[w] = w < NW ? v[w % NW] : 0u;
+            for (int w = 0; w < W; ++w) d[w] = w < NW ? v[w % NW] : 0u;
         }
-        warp_advance<NW>(psets0, tables, 0, v, q.n, lane);
+        if (psets0) warp_advance<NW>(psets0, tables, 0, v, q.n, lane);
+        else warp_advance_tables<NW>(tables, v, q.n, lane);
     }
     if (lane == 0) {
 #pragma unroll
@@ -85,29 +105,41 @@ __device__ void admit_chain(const u32 *psets0, const u32 *tables, u32 *cstate, c
     }
 }
 
+__device__ __forceinline__ void admit_engine(const Tables4 &T, const Tables4 &P0, u32 engine, u32 *cs,
+                                             const AdmitReq *reqs, u32 first, u32 count, unsigned char *rslots,
+                                             u32 sw, int lane)
+{
+    switch (engine) {
+    case ENG_XOSHIRO256: admit_chain<8>(P0.t[0], T.t[0], cs, reqs, first, count, rslots, sw, lane); break;
+    case ENG_XOROSHIRO64:
+        admit_chain<2>(P0.t[engine], T.t[engine], cs, reqs, first, count, rslots, sw, lane);
+        break;
+    case ENG_XOSHIRO512: admit_chain<16>(nullptr, T.t[engine], cs, reqs, first, count, rslots, sw, lane); break;
+    case ENG_XOROSHIRO1024:
+        admit_chain<32>(nullptr, T.t[engine], cs, reqs, first, count, rslots, sw, lane);
+        break;
+    default: admit_chain<4>(P0.t[engine], T.t[engine], cs, reqs, first, count, rslots, sw, lane); break;
+    }
+}
+
 // One warp per client of the round.
 __global__ void k_admit(Tables4 T, Tables4 P0, const AdmitClient *clients, u32 nclients, const AdmitReq *reqs,
-                        u32 *cstates, unsigned char *rslots)
+                        u32 *cstates, unsigned char *rslots, u32 sw)
 {
     const u32 i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= nclients) return;
     const AdmitClient c = clients[i];
-    u32 *cs = cstates + (size_t)c.client * 8;
-    if (c.engine == 0) admit_chain<8>(P0.t[0], T.t[0], cs, reqs, c.first, c.count, rslots, lane);
-    else if (c.engine == ENG_XOROSHIRO64) admit_chain<2>(P0.t[c.engine], T.t[c.engine], cs, reqs, c.first, c.count, rslots, lane);
-    else admit_chain<4>(P0.t[c.engine], T.t[c.engine], cs, reqs, c.first, c.count, rslots, lane);
+    admit_engine(T, P0, c.engine, cstates + (size_t)c.client * sw, reqs, c.first, c.count, rslots, sw, lane);
 }
 
 // The admit step of one request, arguments by value (plain mode); one warp.
-__global__ void k_admit_one(Tables4 T, Tables4 P0, u32 client, u32 engine, u64 n, u32 *cstates, unsigned char *slot)
+__global__ void k_admit_one(Tables4 T, Tables4 P0, u32 client, u32 engine, u64 n, u32 *cstates, unsigned char *slot,
+                            u32 sw)
 {
     const AdmitReq q{n, 0};
     const int lane = threadIdx.x & 31;
-    u32 *cs = cstates + (size_t)client * 8;
-    if (engine == 0) admit_chain<8>(P0.t[0], T.t[0], cs, &q, 0, 1, slot, lane);
-    else if (engine == ENG_XOROSHIRO64) admit_chain<2>(P0.t[engine], T.t[engine], cs, &q, 0, 1, slot, lane);
-    else admit_chain<4>(P0.t[engine], T.t[engine], cs, &q, 0, 1, slot, lane);
+    admit_engine(T, P0, engine, cstates + (size_t)client * sw, &q, 0, 1, slot, sw, lane);
 }
 
 }  // namespace xr
@@ -208,6 +240,7 @@ struct xr_server {
     xr_server_config cfg{};
     std::vector<int> cvar;
     u32 *d_cstates = nullptr;
+    u32 sw = 8;  // words per client state, segment state and request slot (the largest client state)
     unsigned char *arena = nullptr;
     Arena alloc;
     std::mutex mu;
@@ -239,15 +272,15 @@ static int sst(cudaError_t e)
 static Tables4 tables_of(xr_ctx *ctx)
 {
     Tables4 T;
-    for (int e = 0; e < NUM_PSET_ENGINES; ++e) T.t[e] = ctx->tables[e];
+    for (int e = 0; e < NUM_ENGINES_H; ++e) T.t[e] = ctx->tables[e];
     return T;
 }
 
-// The single-step power sets (distance 2^0) of every engine.
+// The single-step power sets (distance 2^0) of every engine that has them.
 static Tables4 steps_of(xr_ctx *ctx)
 {
     Tables4 T;
-    for (int e = 0; e < NUM_PSET_ENGINES; ++e) T.t[e] = pset_sets(ctx, e, pset_index(e, 0));
+    for (int e = 0; e < NUM_ENGINES_H; ++e) T.t[e] = e < NUM_PSET_ENGINES ? pset_sets(ctx, e, pset_index(e, 0)) : nullptr;
     return T;
 }
 
@@ -308,6 +341,7 @@ static cudaError_t launch_round(xr_server *s, Round &R)
     // The plan first: admission writes each request's start state straight
     // into its first segment state (seg_base), so the round needs no seed step.
     build_plan(R.reqs.data(), R.reqs.size(), R.plan);
+    R.plan.slot_words = s->sw;  // admission writes segment states at the server's stride
     // admit arrays, grouped by client in submission order
     R.aclients.clear();
     R.areqs.clear();
@@ -340,7 +374,7 @@ static cudaError_t launch_round(xr_server *s, Round &R)
     const u32 nc = (u32)R.aclients.size();
     k_admit<<<(nc + 3) / 4, 128, 0, s->admit_st>>>(tables_of(s->ctx), steps_of(s->ctx), (const AdmitClient *)recs,
                                                    nc, (const AdmitReq *)(recs + roff), s->d_cstates,
-                                                   (unsigned char *)R.dev.segstates);
+                                                   (unsigned char *)R.dev.segstates, s->sw);
     count_launch();
     err = cudaGetLastError();
     if (err == cudaSuccess) err = cudaEventRecord(R.admitted, s->admit_st);
@@ -358,9 +392,9 @@ static cudaError_t launch_round(xr_server *s, Round &R)
 // `q` is a copy taken under the lock.
 static cudaError_t launch_plain(xr_server *s, const SReq &q, int ev, int slot)
 {
-    unsigned char *sl = s->d_plain_slots + (size_t)slot * 32;
+    unsigned char *sl = s->d_plain_slots + (size_t)slot * s->sw * 4;
     k_admit_one<<<1, 32, 0, s->plain_st>>>(tables_of(s->ctx), steps_of(s->ctx), q.client,
-                                            (u32)engine_of(s->cvar[q.client]), q.n, s->d_cstates, sl);
+                                            (u32)engine_of(s->cvar[q.client]), q.n, s->d_cstates, sl, s->sw);
     count_launch();
     cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess) {
@@ -505,20 +539,26 @@ extern "C" int xr_server_create(xr_ctx *ctx, const xr_server_config *cfg, const 
     if (cfg->mode != XR_SERVE_BATCHED && cfg->mode != XR_SERVE_PLAIN) return XR_EINVAL;
     if (cfg->outputs_per_row && batch_smem_bytes(cfg->outputs_per_row, cfg->block ? cfg->block : 128) > 227 * 1024)
         return XR_EINVAL;
+    u32 sw = 8;
     for (u32 c = 0; c < cfg->nclients; ++c) {
         if (h_client_variants[c] < 0 || h_client_variants[c] >= XR_NUM_VARIANTS) return XR_EINVAL;
-        if (engine_of(h_client_variants[c]) >= NUM_PSET_ENGINES) return XR_EUNSUPPORTED;  // states over 32 bytes
+        sw = std::max(sw, slot_words_of(h_client_variants[c]));
+    }
+    DeviceScope dscope(ctx->device);
+    for (u32 c = 0; c < cfg->nclients; ++c) {  // the large engines' tables are built on first use
+        const int erc = ensure_engine(ctx, engine_of(h_client_variants[c]));
+        if (erc != XR_OK) return erc;
     }
     xr_server *s = new xr_server();
     s->ctx = ctx;
     s->cfg = *cfg;
+    s->sw = sw;
     s->cvar.assign(h_client_variants, h_client_variants + cfg->nclients);
     s->alloc.init(cfg->arena_bytes);
-    DeviceScope dscope(ctx->device);
     cudaError_t err = cudaSuccess;
     int *d_var = nullptr;
     u64 *d_seed = nullptr;
-    if (err == cudaSuccess) err = cudaMalloc((void **)&s->d_cstates, (size_t)cfg->nclients * 32);
+    if (err == cudaSuccess) err = cudaMalloc((void **)&s->d_cstates, (size_t)cfg->nclients * sw * 4);
     if (err == cudaSuccess) err = cudaMalloc((void **)&s->arena, cfg->arena_bytes);
     if (err == cudaSuccess) err = cudaMalloc((void **)&d_var, (size_t)cfg->nclients * sizeof(int));
     if (err == cudaSuccess) err = cudaMalloc((void **)&d_seed, (size_t)cfg->nclients * sizeof(u64));
@@ -527,7 +567,7 @@ extern "C" int xr_server_create(xr_ctx *ctx, const xr_server_config *cfg, const 
     if (err == cudaSuccess)
         err = cudaMemcpy(d_seed, h_client_seeds, (size_t)cfg->nclients * sizeof(u64), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) {
-        k_server_seed<<<(cfg->nclients + 127) / 128, 128>>>(d_var, d_seed, cfg->nclients, s->d_cstates);
+        k_server_seed<<<(cfg->nclients + 127) / 128, 128>>>(d_var, d_seed, cfg->nclients, sw, s->d_cstates);
         count_launch();
         err = cudaGetLastError();
     }
@@ -544,7 +584,7 @@ extern "C" int xr_server_create(xr_ctx *ctx, const xr_server_config *cfg, const 
             err = cudaStreamCreateWithFlags(&R.st, cudaStreamNonBlocking);
             if (err == cudaSuccess) err = cudaEventCreateWithFlags(&R.admitted, cudaEventDisableTiming);
             if (err == cudaSuccess) err = cudaEventCreateWithFlags(&R.done, cudaEventDisableTiming);
-            if (err == cudaSuccess) err = cudaMalloc((void **)&R.d_slots, (size_t)cfg->max_round_requests * 32);
+            if (err == cudaSuccess) err = cudaMalloc((void **)&R.d_slots, (size_t)cfg->max_round_requests * sw * 4);
             // host staging of the admission records for the largest round (a
             // round has at most as many clients as requests); they travel to
             // the device inside the plan upload
@@ -555,11 +595,13 @@ extern "C" int xr_server_create(xr_ctx *ctx, const xr_server_config *cfg, const 
             }
             // size the plan buffers for the largest round up front
             if (err == cudaSuccess) {
-                R.dev.seg_cap = segcap * 32;
+                R.dev.seg_cap = segcap * sw * 4;
                 err = cudaMalloc((void **)&R.dev.segstates, R.dev.seg_cap);
             }
             if (err == cudaSuccess) {
-                R.dev.blob_cap = (size_t)cfg->max_round_requests * 160 + segcap / 32 * 8 * 2 + R.admit_cap + (1 << 20);
+                // + tree items of the large engines: one per request and level
+                R.dev.blob_cap = (size_t)cfg->max_round_requests * (sw > 8 ? 160 + 24 * sizeof(BTreeItem) : 160) +
+                                 segcap / 32 * 8 * 2 + R.admit_cap + (1 << 20);
                 err = cudaMalloc((void **)&R.dev.blob, R.dev.blob_cap);
                 if (err == cudaSuccess) err = cudaMallocHost((void **)&R.dev.pinned, R.dev.blob_cap);
             }
@@ -571,7 +613,7 @@ extern "C" int xr_server_create(xr_ctx *ctx, const xr_server_config *cfg, const 
             err = cudaEventCreateWithFlags(&s->plain_events[i], cudaEventDisableTiming);
             s->free_plain.push_back(i);
         }
-        if (err == cudaSuccess) err = cudaMalloc((void **)&s->d_plain_slots, (size_t)PLAIN_DEPTH * (32 + 64));
+        if (err == cudaSuccess) err = cudaMalloc((void **)&s->d_plain_slots, (size_t)PLAIN_DEPTH * sw * 4);
     }
     if (err != cudaSuccess) {
         xr_server_destroy(s);
@@ -675,8 +717,10 @@ extern "C" int xr_server_client_state(xr_server *s, uint32_t client, void *h_wor
     if (!s || !h_words || client >= s->cfg.nclients) return XR_EINVAL;
     DeviceScope dscope(s->ctx->device);
     cudaError_t err = cudaStreamSynchronize(s->admit_st);
-    unsigned char buf[32];
-    if (err == cudaSuccess) err = cudaMemcpy(buf, s->d_cstates + (size_t)client * 8, 32, cudaMemcpyDeviceToHost);
+    unsigned char buf[XR_MAX_STATE_BYTES];
+    if (err == cudaSuccess)
+        err = cudaMemcpy(buf, s->d_cstates + (size_t)client * s->sw, (size_t)xr_state_bytes(s->cvar[client]),
+                         cudaMemcpyDeviceToHost);
     if (err != cudaSuccess) return sst(err);
     memcpy(h_words, buf, (size_t)xr_state_bytes(s->cvar[client]));
     return XR_OK;

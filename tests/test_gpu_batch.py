@@ -27,10 +27,10 @@ def ctx(xr):
     c.close()
 
 
-def slot_state(name, slots_np, slot):
-    """Oracle words of a 32-byte slot (uint8 numpy array of all slots)."""
+def slot_state(name, slots_np, slot, slot_bytes=32):
+    """Oracle words of a state slot (uint8 numpy array of all slots)."""
     k, w = O.state_words(name), O.word_bits(name)
-    b = slots_np[slot * 32: slot * 32 + k * w // 8].tobytes()
+    b = slots_np[slot * slot_bytes: slot * slot_bytes + k * w // 8].tobytes()
     return np.frombuffer(b, dtype=np.uint32 if w == 32 else np.uint64).astype(np.uint64)
 
 
@@ -40,11 +40,11 @@ def request_view(out_np, off, n, dtype):
     return out_np[off: off + n * es].view(npd)
 
 
-def small_mix(nreq, max_len, seed):
+def small_mix(nreq, max_len, seed, variants=W.SLOT_VARIANTS):
     rng = np.random.default_rng(seed)
     specs = []
     for r in range(nreq):
-        name = W.SLOT_VARIANTS[int(rng.integers(0, len(W.SLOT_VARIANTS)))]
+        name = variants[int(rng.integers(0, len(variants)))]
         dt = [W.native_dtype(name), "f64", "f32"][int(rng.integers(0, 3))]
         n = int(np.clip(np.floor(np.exp(rng.uniform(0, np.log(max_len + 1)))), 0, max_len))
         if r % 17 == 0:
@@ -58,7 +58,7 @@ def run_batch(xr, ctx, specs, seeds, use_graph=False, tune=False, reps=1):
     reqs, offs, arena = xr.pack_requests(specs)
     b = xr.Batch(ctx, reqs)
     assert b.arena_bytes <= arena
-    slots = torch.zeros(len(specs) * 32, dtype=torch.uint8, device="cuda")
+    slots = torch.zeros(len(specs) * b.slot_bytes, dtype=torch.uint8, device="cuda")
     out = torch.full((max(arena, 16),), 0x5A, dtype=torch.uint8, device="cuda")
     d_seeds = torch.tensor(seeds, dtype=torch.int64, device="cuda") if seeds is not None else None
     if tune:
@@ -152,11 +152,13 @@ def test_batch_every_config(ctx, xr, opt, block, align):
     bulk copies everywhere)."""
     import torch
     specs = small_mix(60, 3000, seed=25) + [("xoshiro256**", "u64", 40000, 60), ("xoshiro128++", "f32", 70000, 61),
-                                            ("xoroshiro128+", "f64", 33 * 1024, 62)]
+                                            ("xoroshiro128+", "f64", 33 * 1024, 62),
+                                            ("xoshiro512+", "f64", 34 * 1024 + 3, 63),
+                                            ("xoroshiro1024++", "u64", 2049, 64)]
     reqs, offs, arena = xr.pack_requests(specs, align=align)
     b = xr.Batch(ctx, reqs)
     b.set_config(opt, block)
-    slots = torch.zeros(len(specs) * 32, dtype=torch.uint8, device="cuda")
+    slots = torch.zeros(len(specs) * b.slot_bytes, dtype=torch.uint8, device="cuda")
     out = torch.zeros(max(arena, 16), dtype=torch.uint8, device="cuda")
     seeds = torch.arange(len(specs), dtype=torch.int64, device="cuda") + 77
     b.run(seeds, slots, out)
@@ -176,9 +178,57 @@ def test_batch_rejects_bad_plans(ctx, xr):
         xr.Batch(ctx, [R(0, 0, 10, 0, 8)])                                # unaligned offset
     with pytest.raises(xr.XRError):
         xr.Batch(ctx, [R(6, 0, 10, 0, 0)])                                # u64 from a 32-bit generator
-    with pytest.raises(xr.XRError) as e:
-        xr.Batch(ctx, [R(xr.VARIANTS["xoshiro512+"], 0, 10, 0, 0)])      # 64-byte state: no slot fits
-    assert e.value.status == xr.XR_EUNSUPPORTED
+
+
+def test_batch_slot_bytes_follow_the_largest_state(ctx, xr):
+    """Slots are 32 bytes unless a request's state is larger: 64 with a
+    xoshiro512 request, 128 with a xoroshiro1024 request."""
+    R, V = xr.Request, xr.VARIANTS
+    for names, want in ((["xoshiro256**", "xoroshiro64*"], 32), (["xoshiro128+", "xoshiro512**"], 64),
+                        (["xoshiro512+", "xoroshiro1024++", "xoroshiro128+"], 128)):
+        b = xr.Batch(ctx, [R(V[nm], 2, 10, k, 256 * k) for k, nm in enumerate(names)])
+        assert b.slot_bytes == want, names
+        b.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_large_states_alone_and_in_the_mix(ctx, xr, use_graph):
+    """Requests of all 18 generators, xoshiro512 and xoroshiro1024 among them
+    (Sec. 3.1 X_kw, Fig. 2; Sec. 3.2 S_8w, Fig. 4), in one batch with
+    128-byte slots: each equals the oracle and the same request alone through
+    xr_fill_seq; the slots hold the advanced states; a second run (a graph
+    replay when use_graph) continues every sequence."""
+    import torch
+    specs = small_mix(160, 70000, seed=26, variants=W.ALL_VARIANTS)
+    specs += [("xoshiro512++", "f64", 40 * 1024, 160), ("xoroshiro1024**", "u64", 33 * 1024 + 5, 161),
+              ("xoroshiro1024*", "f32", 1, 162), ("xoshiro512**", "u64", 300000, 163)]
+    seeds = [3 * r + 11 for r in range(len(specs))]
+    b, offs, out, slots = run_batch(xr, ctx, specs, seeds, use_graph=use_graph)
+    assert b.slot_bytes == 128
+    for r, (name, dt, n, slot) in enumerate(specs):
+        raw, after = O.generate(name, O.seed(name, seeds[r]), n)
+        assert_bits_equal(request_view(out, offs[r], n, dt), expected(name, raw, dt), "request %d %s" % (r, name))
+        assert (slot_state(name, slots, slot, 128) == after).all(), (r, name)
+        st = ctx.empty_states(name, 1)
+        ctx.seed(name, seeds[r], st)
+        alone = ctx.empty_output(max(n, 1), dt)
+        ctx.fill_seq(name, st, n, dt, alone)
+        torch.cuda.synchronize()
+        got = request_view(out, offs[r], n, dt)
+        assert_bits_equal(got, alone.cpu().numpy().view(got.dtype)[:n], "request %d alone" % r)
+    # second run from the advanced slots
+    d_slots = torch.from_numpy(slots.copy()).cuda()
+    d_out = torch.zeros(len(out), dtype=torch.uint8, device="cuda")
+    b.run(None, d_slots, d_out, use_graph=use_graph)
+    torch.cuda.synchronize()
+    o2 = d_out.cpu().numpy()
+    for r, (name, dt, n, slot) in enumerate(specs):
+        if n > 5000 and r % 7:
+            continue   # the oracle's 2n outputs of the long ones: a sample suffices
+        raw, _ = O.generate(name, O.seed(name, seeds[r]), 2 * n)
+        assert_bits_equal(request_view(o2, offs[r], n, dt), expected(name, raw[n:], dt), "request %d run 2" % r)
+    assert ctx.status() == 0
+    b.close()
 
 
 def test_batch_configuration_sampled(ctx, xr):

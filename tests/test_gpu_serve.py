@@ -34,12 +34,12 @@ CLIENTS = ["xoshiro256**", "xoroshiro128++", "xoshiro256+", "xoroshiro128**", "x
            "xoshiro256++", "xoroshiro128+", "xoroshiro128*", "xoroshiro64**"]
 
 
-def mixed_trace(nreq, seed, max_len=1 << 17):
+def mixed_trace(nreq, seed, max_len=1 << 17, clients=CLIENTS):
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(nreq):
-        c = int(rng.integers(0, len(CLIENTS)))
-        name = CLIENTS[c]
+        c = int(rng.integers(0, len(clients)))
+        name = clients[c]
         dt = [W.native_dtype(name), "f64", "f32"][int(rng.integers(0, 3))]
         n = int(np.floor(np.exp(rng.uniform(0, np.log(max_len)))))
         out.append((c, max(n, 1), dt))
@@ -49,12 +49,13 @@ def mixed_trace(nreq, seed, max_len=1 << 17):
 class Expect:
     """Each client's sequence from its SplitMix64 seed, consumed in order."""
 
-    def __init__(self, seeds):
-        self.state = {c: O.seed(name, seeds[c]) for c, name in enumerate(CLIENTS)}
+    def __init__(self, seeds, clients=CLIENTS):
+        self.clients = clients
+        self.state = {c: O.seed(name, seeds[c]) for c, name in enumerate(clients)}
 
     def take(self, c, n, dt):
-        raw, self.state[c] = O.generate(CLIENTS[c], self.state[c], n)
-        return expected(CLIENTS[c], raw, dt)
+        raw, self.state[c] = O.generate(self.clients[c], self.state[c], n)
+        return expected(self.clients[c], raw, dt)
 
 
 def read(srv, off, n, dt, torch):
@@ -158,9 +159,36 @@ def test_rejects_bad_requests(ctx, xr):
             srv.submit(0, 1 << 20, "u64")                # larger than the arena
         with pytest.raises(xr.XRError):
             srv.release(12345)
-    with pytest.raises(xr.XRError) as e:
-        xr.Server(ctx, ["xoroshiro1024++"], [1], arena_bytes=1 << 20)   # 128-byte state: no slot fits
-    assert e.value.status == xr.XR_EUNSUPPORTED
+
+
+LARGE_CLIENTS = ["xoroshiro1024++", "xoshiro512**", "xoshiro256**", "xoroshiro1024*", "xoshiro512+",
+                 "xoroshiro64*", "xoshiro128++", "xoroshiro1024**"]
+
+
+@pytest.mark.parametrize("mode", ["batched", "plain"])
+def test_large_state_clients(ctx, xr, mode):
+    """Clients of xoshiro512 and xoroshiro1024 (64- and 128-byte states, Sec.
+    3.1 X_kw and Sec. 3.2 S_8w) served beside smaller ones: every output is
+    the client's next values, and each client's resident state has moved on
+    by exactly its requests."""
+    import torch
+    seeds = [40 + c for c in range(len(LARGE_CLIENTS))]
+    trace = mixed_trace(120, seed=33, max_len=1 << 16, clients=LARGE_CLIENTS)
+    trace += [(0, 70000, "f64"), (1, 3 * 1024, "u64"), (3, 1, "f32")]
+    exp = Expect(seeds, LARGE_CLIENTS)
+    with xr.Server(ctx, LARGE_CLIENTS, seeds, arena_bytes=256 << 20, mode=mode, max_rounds=3,
+                   max_round_requests=32) as srv:
+        for burst in range(0, len(trace), 30):
+            tickets = [(srv.submit(c, n, dt), c, n, dt) for (c, n, dt) in trace[burst:burst + 30]]
+            for t, c, n, dt in tickets:
+                off, _ = srv.wait(t)
+                assert_bits_equal(read(srv, off, n, dt, torch), exp.take(c, n, dt),
+                                  "%s client %d n=%d" % (LARGE_CLIENTS[c], c, n))
+                srv.release(t)
+        for c, name in enumerate(LARGE_CLIENTS):
+            want = exp.state[c].astype(np.uint32 if O.word_bits(name) == 32 else np.uint64).tobytes()
+            assert srv.client_state(c) == want, name
+    assert ctx.status() == 0
 
 
 def test_serving_trace_sampled(ctx, xr):
