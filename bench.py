@@ -35,6 +35,7 @@ import workloads as W  # noqa: E402
 METRIC = "generated GB/s & % of HBM roofline (batched vs plain, 1 GB300); p50/p99 latency"
 UNIT = "GB/s"
 FILL_SOURCES = ("paper_1805_01407_gb300/csrc/xr_fill_impl.cuh", "paper_1805_01407_gb300/csrc/xr_device.cuh")
+FUSED_SOURCES = FILL_SOURCES + ("paper_1805_01407_gb300/csrc/xr_fill_streams.cuh", "paper_1805_01407_gb300/csrc/xr_f2.cuh")
 
 
 def parse_args():
@@ -185,9 +186,9 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def fill_source_hash():
+def fill_source_hash(sources=FILL_SOURCES):
     h = hashlib.sha256()
-    for p in FILL_SOURCES:
+    for p in sources:
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -209,6 +210,26 @@ def recorded_traffic():
         return {"bytes_per_launch": float(kv["dram_bytes_per_launch_full_size"]),
                 "algorithmic_bytes_per_launch": float(kv.get("algorithmic_bytes_per_launch", "nan")),
                 "note": kv.get("scaling", "")}
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def recorded_fused_counts():
+    """Integer ALU lane operations and shared-memory wavefronts per stream of
+    the fused stream-start fill (xoshiro256++, 64 u64 outputs), from the
+    committed ncu summary, if taken on the current sources; else None."""
+    path = os.path.join(ROOT, "profiles", "fill_streams__xoshiro256pp_2p21x64.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#") and not line.startswith(" "):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha") != fill_source_hash(FUSED_SOURCES):
+            return None
+        return {"alu_lane_ops_per_stream": float(kv["alu_lane_ops_per_stream"]),
+                "shared_wavefronts_per_stream": float(kv["shared_wavefronts_per_stream"])}
     except (OSError, KeyError, ValueError):
         return None
 
@@ -565,7 +586,7 @@ def run_xr(args):
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             line["extra_generators"]["cpu_baseline"] = extra_cpu_baseline()
     if not args.no_jumpstart:
-        line["jumpstart"] = run_jumpstart(xr, ctx, args)
+        line["jumpstart"] = run_jumpstart(xr, ctx, args, wc, ac)
     if not args.no_analysis:
         line["analysis"] = run_analysis(xr, ctx, args)
     if not args.no_e2e:
@@ -748,7 +769,7 @@ def run_analysis(xr, ctx, args):
     return res
 
 
-def run_jumpstart(xr, ctx, args):
+def run_jumpstart(xr, ctx, args, wc, ac):
     """Jump-start at scale: 2^24 xoshiro256++ streams J^i(s0) and L^i(s0) from
     SplitMix64(42), then 64 u64 outputs each; stream starts and fill timed
     with events on their stream (median of 3), then both pipelined over 16
@@ -813,10 +834,32 @@ def run_jumpstart(xr, ctx, args):
                      "pipelined_chunks": chunks, "pipelined_same_output": same,
                      "fused_ms": ms_fused, "fused_gbs": S * m * 8 / (ms_fused / 1e3) / 1e9,
                      "fused_frac_of_measured_peak": S * m * 8 / (ms_fused / 1e3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
-                     "fused_same_output": same_fused}
+                     "fused_same_output": same_fused,
+                     "fused_roofline": fused_roofline(S, m, ms_fused, wc, ac)}
     del out, states
     torch.cuda.synchronize()
     assert ctx.status() == 0
+    return res
+
+
+def fused_roofline(S, m, ms, wc, ac):
+    """The fused kernel's three bounds for S streams x m u64 outputs: output
+    bytes at the measured write peak, its ALU lane operations at the measured
+    ALU peak, and its shared-memory wavefronts at one per cycle per SM (max
+    SM clock); the slowest binds."""
+    import torch
+    counts = recorded_fused_counts()
+    hbm_ms = S * m * 8 / (wc["write_peak_gbs"] * 1e9) * 1e3
+    res = {"hbm_ms": hbm_ms}
+    if counts:
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        res["alu_ms"] = S * counts["alu_lane_ops_per_stream"] / ac["alu_lane_ops_per_s"] * 1e3
+        res["l1_ms"] = S * counts["shared_wavefronts_per_stream"] / (sms * 2.07e9) * 1e3
+        res.update(counts)
+    bound = max((v, k[:-3]) for k, v in res.items() if k.endswith("_ms"))
+    res.update(bound=bound[1], roofline_ms=bound[0], frac=bound[0] / ms,
+               source="profiles/fill_streams__xoshiro256pp_2p21x64.txt" if counts else
+               "counts not recorded for the current sources: HBM bound only")
     return res
 
 
@@ -886,6 +929,7 @@ def run_e2e(ctx, args, first, bytes_per_step, world, dist):
         torch.cuda.synchronize()
         times.append(max_over_ranks(time.perf_counter() - t0, dist, "cuda"))
     link_after = d2h_link_gbs(h_out)
+    chunks = d2h_chunks_gbs(h_out)
     h2d = sum(len(host_base[v]) for v, _ in jobs())
     per_step = [world * bytes_per_step / t / 1e9 for t in times]
     value = statistics.median(per_step)
@@ -898,8 +942,61 @@ def run_e2e(ctx, args, first, bytes_per_step, world, dist):
             "bound": {"d2h_link_gbs": link, "d2h_link_before_after_gbs": [link_before, link_after],
                       "frac": value / world / link, "frac_spread": [min(per_step) / world / link,
                                                                     max(per_step) / world / link],
+                      "d2h_per_gib_chunk_gbs": chunks,
+                      "host_buffer_page_nodes": host_page_nodes(h_out),
+                      "staging_chunk_bytes": 256 << 20,
                       "what": "device-to-pinned-host copy bandwidth of this GPU, 1 GiB copies timed with events, "
                               "before and after the end-to-end steps"}}
+
+
+def host_page_nodes(t, samples=64):
+    """NUMA node of `samples` pages spread over a host tensor (move_pages with
+    no target nodes only reports where each page is): {node: count}."""
+    import ctypes
+    import platform
+    nr = {"x86_64": 279, "aarch64": 239}.get(platform.machine())  # the move_pages system call
+    if nr is None:
+        return None
+    try:
+        libc = ctypes.CDLL(None, use_errno=True)
+        page = os.sysconf("SC_PAGE_SIZE")
+        base, nbytes = t.data_ptr(), t.numel() * t.element_size()
+        addrs = [(base + k * (nbytes // samples)) // page * page for k in range(samples)]
+        pages = (ctypes.c_void_p * samples)(*addrs)
+        status = (ctypes.c_int * samples)()
+        libc.syscall.restype = ctypes.c_long
+        if libc.syscall(ctypes.c_long(nr), ctypes.c_int(0), ctypes.c_ulong(samples), pages, None, status,
+                        ctypes.c_int(0)) != 0:
+            return None
+        hist = {}
+        for st in status:
+            hist[str(st)] = hist.get(str(st), 0) + 1
+        return hist
+    except (OSError, AttributeError):
+        return None
+
+
+def d2h_chunks_gbs(h_out, chunk=1 << 30):
+    """Device-to-host copy rate into each 1 GiB piece of the pinned buffer
+    (median of 3 each), to see whether the whole buffer sits behind the same
+    link."""
+    import torch
+    src = torch.empty(chunk, dtype=torch.uint8, device="cuda")
+    src.fill_(1)
+    stream = torch.cuda.current_stream()
+    res = []
+    for off in range(0, h_out.numel() - chunk + 1, chunk):
+        ts = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h_out[off:off + chunk].copy_(src, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        res.append(chunk / (statistics.median(ts) / 1e3) / 1e9)
+    del src
+    return res
 
 
 def d2h_link_gbs(h_out):

@@ -18,8 +18,9 @@ namespace xr {
 // 32 consecutive streams (rows p0 + P j ..), written by 2D tile stores like
 // k_fill_tma.  The start states never reach global memory.  A warp takes
 // FS_GROUPS groups of 32 parents in turn, so the tile stores of one group
-// drain while the next group's products run, and keeps a lane's start state
-// in a shared-memory slot for the rare exact redo of a double row.  One tile
+// drain while the next group's products run; for doubles of 64-bit words a
+// lane also keeps its start state in a shared-memory slot, for the rare exact
+// redo of a row.  One tile
 // per warp and 16 warps per CTA measured best (2^24 x 64: u64 1.63 ms, f64
 // 1.81 ms; 8 warps x 1 tile 1.64 / 1.88 ms; 8 warps x 2 tiles, u64 1.73 ms):
 // shared memory, not the store queue, limits the warps per SM.  Only rows
@@ -83,10 +84,22 @@ __global__ void __launch_bounds__(FS_WARPS * 32)
             }
         }
         russians_matvec<NW>(T, v, r);
+        // the start state goes to the lane's slot only where a row may need
+        // its exact redo (doubles of 64-bit words); the engine takes it from
+        // registers
+        if constexpr (DT == DT_F64 && sizeof(typename G::word) == 8) {
 #pragma unroll
-        for (int w = 0; w < NW; ++w) reinterpret_cast<u32 *>(slot)[w] = r[w];
+            for (int q = 0; q < NW / 4; ++q)
+                reinterpret_cast<uint4 *>(slot)[q] = make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+        }
         E e;
-        load_state(e, slot);
+        if constexpr (sizeof(typename E::word) == 8) {
+#pragma unroll
+            for (int k = 0; k < E::K; ++k) e.s[k] = (u64)r[2 * k] | ((u64)r[2 * k + 1] << 32);
+        } else {
+#pragma unroll
+            for (int k = 0; k < E::K; ++k) e.s[k] = r[k];
+        }
         if (live && state_is_zero(e)) atomicCAS(status, 0, XR_EZERO_STATE);
         for (size_t j0 = 0; j0 < m; j0 += COLS, ++it) {
             const u32 tile = tiles + (u32)((it % FS_NBUF) * TILE_BYTES);
