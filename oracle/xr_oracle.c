@@ -18,9 +18,11 @@
  *     Table 7 (32-bit engines), Table 8 (32-bit scramblers); word choices from
  *     the code figures of Sec. 3 and the remark in Sec. 5.2 that the 32-bit
  *     xoshiro128 uses the words of xoshiro256;
- *   - seeding with SplitMix64 (Sec. 5.3; the mixer is defined in Steele, Lea
- *     and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014,
- *     and is not printed in the paper: parity unpinned for its constants);
+ *   - seeding with SplitMix64 (Sec. 5.3; the paper cites Steele, Lea and
+ *     Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014,
+ *     and prints no definition: the Weyl increment is the odd integer nearest
+ *     2^64 / phi and the finalizer Stafford's variant 13, both pinned by the
+ *     tests against values derived or implemented independently of this file);
  *   - doubles from the upper 53 bits (Sec. 5.3, "(x >> 11) * 2^-53");
  *   - F2 matrices T (transition as a map on column vectors of state bits), the
  *     characteristic polynomial (Sec. 6), Berlekamp-Massey (Sec. 6, Sec. 9.3),

@@ -401,7 +401,8 @@ def test_starstar_parameters_from_section_10():
     w-r .. w-1 down to 0 .. r-1, and the multiplier 2^t+1 leaves the t lowest bits
     alone, so bits 0 .. t-1 of z are bits w-r .. w-r+t-1 of x(2^s+1)."""
     rng = random.Random(10)
-    for name, w, word in (("xoshiro256**", 64, 1), ("xoroshiro128**", 64, 0), ("xoshiro128**", 32, 1)):
+    for name, w, word in (("xoshiro256**", 64, 1), ("xoroshiro128**", 64, 0), ("xoshiro128**", 32, 1),
+                          ("xoshiro512**", 64, 1), ("xoroshiro1024**", 64, 0)):
         for _ in range(2000):
             s = rand_state(name, rng)
             z = O.scramble(name, s)
@@ -429,15 +430,32 @@ def test_xoroshiro64_starstar_parameters():
 
 def test_plusplus_low_bit():
     """Sec. 4.3 / 10.3: z = rotl(x + y, r) + x; bit 0 of z is bit (w - r) of x + y
-    xor bit 0 of x (rotations 23, 17, 7 from Tables 5 and 8)."""
+    xor bit 0 of x (rotations 23, 17, 7 from Tables 5 and 8; xoshiro512++ adds
+    s2 after the rotation, xoroshiro1024++ the last word s15)."""
     rng = random.Random(13)
     for name, w, r, (p, q) in (("xoshiro256++", 64, 23, (0, 3)), ("xoroshiro128++", 64, 17, (0, 1)),
-                               ("xoshiro128++", 32, 7, (0, 3))):
+                               ("xoshiro128++", 32, 7, (0, 3)), ("xoshiro512++", 64, 17, (2, 0)),
+                               ("xoroshiro1024++", 64, 23, (15, 0))):
         for _ in range(2000):
             s = rand_state(name, rng)
             z = O.scramble(name, s)
             sm = (int(s[p]) + int(s[q])) % 2**w
             assert z & 1 == ((sm >> (w - r)) ^ int(s[p])) & 1
+
+
+def test_plus_sums_the_plusplus_pair():
+    """Sec. 4.1 and 4.3: the + and ++ scramblers of an engine sum the same two
+    words (the code figures of Sec. 3), ++ then rotating and adding one of
+    them.  So the + output is rotr(z++ - x, r) on the same state, which ties
+    the + word pair to the ++ one pinned by the low-bit test above."""
+    rng = random.Random(15)
+    for plus, pp, w, r, p in (("xoshiro256+", "xoshiro256++", 64, 23, 0), ("xoroshiro128+", "xoroshiro128++", 64, 17, 0),
+                              ("xoshiro128+", "xoshiro128++", 32, 7, 0), ("xoshiro512+", "xoshiro512++", 64, 17, 2)):
+        M = 2**w - 1
+        for _ in range(1000):
+            s = rand_state(plus, rng)
+            y = (O.scramble(pp, s) - int(s[p])) & M
+            assert O.scramble(plus, s) == ((y >> r) | (y << (w - r))) & M, plus
 
 
 def test_star_low_bits():
@@ -454,6 +472,33 @@ def test_star_low_bits():
         assert z & 1 == x & 1 and (z >> 1) & 1 == ((x >> 1) ^ x) & 1
 
 
+def test_star_multipliers_from_the_golden_ratio():
+    """Sec. 4.2: the * multiplier is close to phi 2^w mod 2^w = 2^w / phi (phi
+    the golden ratio), its low bits adjusted so that bit 1 is set.  With the
+    scrambled word equal to 1 the * output is the multiplier itself, so the
+    oracle's constant is read back and compared with 2^w / phi computed from
+    an exact integer square root (within the few units the adjustment of the
+    lowest bits allows), with bits 0 and 1 set, and with the values printed in
+    Tables 5 and 8.  A wrong digit anywhere fails."""
+    import math
+    for name, w, k, printed in (("xoroshiro128*", 64, 2, 0x9e3779b97f4a7c13),
+                                ("xoroshiro1024*", 64, 16, 0x9e3779b97f4a7c13),
+                                ("xoroshiro64*", 32, 2, 0x9E3779BB)):
+        # 2^w / phi = (sqrt(5) - 1) 2^(w-1), scaled by 2^(w+1) to stay an integer: exact to < 1 unit
+        golden_x = math.isqrt(5 << (4 * w)) - (1 << (2 * w))
+        # the scrambled word is word 0 of the state in the oracle's order
+        s = np.zeros(k, np.uint64)
+        s[0] = 1
+        m = O.scramble(name, s)
+        assert m == printed, (name, hex(m))
+        assert m & 3 == 3, name
+        assert abs(m * 2 ** (w + 1) - golden_x) < 4 * 2 ** (w + 1), (name, hex(m))
+    # xoroshiro64** takes the same first multiplier (Table 8)
+    s = np.zeros(2, np.uint64)
+    s[0] = 1
+    assert O.scramble("xoroshiro64**", s) == (((0x9E3779BB << 5) | (0x9E3779BB >> 27)) & 0xffffffff) * 5 % 2**32
+
+
 def test_output_precedes_update():
     """Sec. 2: the scrambler reads the current state, before the engine step."""
     for name in O.VARIANTS:
@@ -464,7 +509,7 @@ def test_output_precedes_update():
         assert (after == O.step(name, s, 2)).all()
 
 
-# --------------------------------------------------------------- SplitMix64 (parity unpinned)
+# --------------------------------------------------------------- SplitMix64 seeding (Sec. 5.3)
 
 def test_splitmix64_properties():
     """Word layout of the seeding (Sec. 5.3): 32-bit states take the low half of
