@@ -3,8 +3,7 @@
 Every integer result is compared bit for bit; doubles and floats are compared
 as bit patterns too (the conversions are exact, Sec. 5.3, so the tolerance is
 zero).  Small shapes cover single values, partial tiles and ragged tails;
-the plain and bulk configurations are compared in full, the 2^24-stream
-jump-start configuration on sampled streams.
+the plain, bulk and jump-start configurations are compared in full.
 """
 import os
 
@@ -341,18 +340,19 @@ def _host_cores():
 
 
 def compare_streams_in_full(name, kind, base, S, m, d_states, outs, slice_streams=1 << 12):
-    """Every start state and every output of S streams J^i(base), i < S,
-    against the oracle.  The device results are copied back slice by slice
-    (slice_streams streams each) by this thread; the oracle computes the
-    matching slices on every host core (worker threads: the oracle's C calls
-    run without the GIL), one single-threaded oracle per slice.  outs maps a
-    dtype to its device output (S * m elements).  Returns the number of
-    values compared."""
+    """Every start state (unless d_states is None) and every output of S
+    streams J^i(base), i < S, against the oracle.  The device results are
+    copied back slice by slice (slice_streams streams each) by this thread;
+    the oracle computes the matching slices on every host core (worker
+    threads: the oracle's C calls run without the GIL), one single-threaded
+    oracle per slice.  outs maps a dtype to its device output (S * m
+    elements).  Returns the number of values compared."""
     from concurrent.futures import ThreadPoolExecutor, wait, FIRST_COMPLETED
 
     def work(s0, cnt, got_states, got):
         st = O.streams(name, kind, base, cnt, first=s0)
-        assert (got_states == st).all(), "%s start states %d..%d" % (name, s0, s0 + cnt)
+        if got_states is not None:
+            assert (got_states == st).all(), "%s start states %d..%d" % (name, s0, s0 + cnt)
         raw = O.fill_streams(name, st, m)
         for dtype, g in got.items():
             assert_bits_equal(g, expected(name, raw, dtype), "%s %s streams %d..%d" % (name, dtype, s0, s0 + cnt))
@@ -363,7 +363,8 @@ def compare_streams_in_full(name, kind, base, S, m, d_states, outs, slice_stream
     with ThreadPoolExecutor(cores) as ex:
         for s0 in range(0, S, slice_streams):
             cnt = min(slice_streams, S - s0)
-            got_states = states_from_device(name, d_states[s0 * len(d_states) // S:(s0 + cnt) * len(d_states) // S])
+            got_states = None if d_states is None else \
+                states_from_device(name, d_states[s0 * len(d_states) // S:(s0 + cnt) * len(d_states) // S])
             got = {dt: out_to_numpy(o[s0 * m:(s0 + cnt) * m], dt) for dt, o in outs.items()}
             pending.add(ex.submit(work, s0, cnt, got_states, got))
             while len(pending) >= 2 * cores:
@@ -398,41 +399,53 @@ def test_bulk_configuration_full(ctx, xr, name):
 
 
 @pytest.mark.parametrize("name", ["xoshiro256**", "xoroshiro128+", "xoshiro128++"])
-def test_bulk_configuration_fused_sampled(ctx, xr, name):
+def test_bulk_configuration_through_fill_streams_full(ctx, xr, name):
     """2^20 streams x 2^10 outputs from SplitMix64(42) through xr_fill_streams
-    (start states computed in the generating threads): 66 sampled streams and
-    the first 64 compared in full, native word and f64."""
+    (its state-table path, for these 8-KiB rows): every value, native word
+    and f64, against the oracle on every host core."""
     import torch
     c = W.CONFIG_BULK
     S, m = c["S"], c["m"]
     base = O.seed(name, c["seed"])
-    d = O.jump_log2(name, c["kind"])
-    idx = sorted(set(range(64)) | set(int(i) for i in W.sample_indices(S, 66, seed=3)))
     d_base = ctx.empty_states(name, 1)
     ctx.seed(name, c["seed"], d_base)
+    outs = {}
     for dtype in (xr.native_dtype(name), "f64"):
-        out = ctx.empty_output(S * m, dtype)
-        ctx.fill_streams(name, c["kind"], d_base, 0, S, m, dtype, out)
-        torch.cuda.synchronize()
-        rows = out.view(S, m)[torch.as_tensor(idx, device="cuda")]
-        got = out_to_numpy(rows.contiguous(), dtype).reshape(len(idx), m)
-        for r, i in enumerate(idx):
-            raw, _ = O.generate(name, O.jump_pow(name, d, int(i), base), m)
-            assert_bits_equal(got[r], expected(name, raw, dtype), "%s %s stream %d" % (name, dtype, i))
-        del out
+        outs[dtype] = ctx.empty_output(S * m, dtype)
+        ctx.fill_streams(name, c["kind"], d_base, 0, S, m, dtype, outs[dtype])
+    torch.cuda.synchronize()
     assert ctx.status() == 0
+    assert compare_streams_in_full(name, c["kind"], base, S, m, None, outs) == 2 * S * m
+    del outs
 
 
 @pytest.mark.parametrize("kind", ["jump", "long"])
-def test_jumpstart_configuration_sampled(ctx, xr, kind):
-    """2^24 xoshiro256++ streams J^i(s0) / L^i(s0), 64 outputs each: 4096
-    sampled streams against the oracle's jump power, and the first 2048 start
-    states against one CPU jump after another."""
+def test_jumpstart_configuration_fused_full(ctx, xr, kind):
+    """The jump-start configuration in full through xr_fill_streams (start
+    states computed in the generating threads, the launch the benchmark
+    times): all 2^24 xoshiro256++ streams J^i(s0) / L^i(s0) x 64 u64 outputs,
+    2^30 values, against one CPU jump after another on every host core."""
     import torch
     c = W.CONFIG_JUMPSTART
     name, S, m = c["variant"], c["S"], c["m"]
     base = O.seed(name, c["seed"])
-    d = O.jump_log2(name, kind)
+    d_base = ctx.empty_states(name, 1)
+    ctx.seed(name, c["seed"], d_base)
+    out = ctx.empty_output(S * m, "u64")
+    ctx.fill_streams(name, kind, d_base, 0, S, m, "u64", out)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    assert compare_streams_in_full(name, kind, base, S, m, None, {"u64": out}, slice_streams=1 << 14) == S * m
+
+
+@pytest.mark.parametrize("kind", ["jump", "long"])
+def test_jumpstart_configuration_two_calls_full(ctx, xr, kind):
+    """The same configuration through xr_make_streams and xr_fill: all 2^24
+    start states of the table and all 2^30 values in full."""
+    import torch
+    c = W.CONFIG_JUMPSTART
+    name, S, m = c["variant"], c["S"], c["m"]
+    base = O.seed(name, c["seed"])
     d_base = ctx.empty_states(name, 1)
     ctx.seed(name, c["seed"], d_base)
     d_states = ctx.empty_states(name, S)
@@ -440,16 +453,8 @@ def test_jumpstart_configuration_sampled(ctx, xr, kind):
     out = ctx.empty_output(S * m, "u64")
     ctx.fill(name, d_states, S, m, "u64", out)
     torch.cuda.synchronize()
-    got_states = states_from_device(name, d_states)
-    assert (got_states[:2048] == O.streams(name, kind, base, 2048)).all()
-    idx = W.sample_indices(S, c["samples"], c["sample_seed"])
-    rows = out_to_numpy(out.view(S, m)[torch.as_tensor(idx, device="cuda")].contiguous(), "u64")
-    rows = rows.reshape(len(idx), m)
-    for r, i in enumerate(idx):
-        st = O.jump_pow(name, d, int(i), base)
-        assert (got_states[i] == st).all(), int(i)
-        raw, _ = O.generate(name, st, m)
-        assert_bits_equal(rows[r], raw, "stream %d" % i)
+    assert ctx.status() == 0
+    assert compare_streams_in_full(name, kind, base, S, m, d_states, {"u64": out}, slice_streams=1 << 14) == S * m
 
 
 # (S, first, m).  Below 512 x 32 streams everything goes through a state
@@ -484,32 +489,6 @@ def test_fill_streams(ctx, xr, name, kind):
             assert_bits_equal(got, expected(name, raw, dtype),
                               "%s %s %s S=%d first=%d m=%d" % (name, kind, dtype, S, first, m))
     assert ctx.status() == 0
-
-
-@pytest.mark.parametrize("kind", ["jump", "long"])
-def test_jumpstart_configuration_fused_sampled(ctx, xr, kind):
-    """The jump-start configuration (2^24 xoshiro256++ streams x 64 u64
-    outputs) through xr_fill_streams: 4096 sampled streams against the
-    oracle's jump power and outputs, and the first 1024 rows in full."""
-    import torch
-    c = W.CONFIG_JUMPSTART
-    name, S, m = c["variant"], c["S"], c["m"]
-    base = O.seed(name, c["seed"])
-    d = O.jump_log2(name, kind)
-    d_base = ctx.empty_states(name, 1)
-    ctx.seed(name, c["seed"], d_base)
-    out = ctx.empty_output(S * m, "u64")
-    ctx.fill_streams(name, kind, d_base, 0, S, m, "u64", out)
-    torch.cuda.synchronize()
-    assert ctx.status() == 0
-    head = out_to_numpy(out[:1024 * m], "u64")
-    assert_bits_equal(head, O.bulk_fill(name, kind, base, 1024, m).reshape(-1), "first 1024 streams")
-    idx = W.sample_indices(S, c["samples"], c["sample_seed"])
-    rows = out_to_numpy(out.view(S, m)[torch.as_tensor(idx, device="cuda")].contiguous(), "u64")
-    rows = rows.reshape(len(idx), m)
-    for r, i in enumerate(idx):
-        raw, _ = O.generate(name, O.jump_pow(name, d, int(i), base), m)
-        assert_bits_equal(rows[r], raw, "stream %d" % i)
 
 
 def test_fill_host_chunks(ctx, xr):
