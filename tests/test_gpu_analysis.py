@@ -168,16 +168,21 @@ def test_linear_complexity_many_rejects_a_bad_job(ctx, xr):
     assert ctx.linear_complexity_many([], st) == []
 
 
-def test_linear_complexity_bulk_configuration_sampled(ctx, xr):
+def test_linear_complexity_bulk_configuration_full(ctx, xr):
     """The bulk configuration (every bit of the 8 bulk generators, 2^16 bits):
-    all 448 sequences in one call, every 8th against the oracle; bit 0 of the
-    + generators has the complexity of Table 13 (n)."""
+    all 448 sequences in one call, every one against the oracle's
+    Berlekamp-Massey (run on every host core: the oracle's C calls release the
+    GIL); bit 0 of the + generators has the complexity of Table 13 (n)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
     c = W.CONFIG_LC_BULK
     jobs = W.lc_bulk_jobs(**c)
     got = ctx.linear_complexity_many(jobs, states_for(ctx, xr, jobs, [c["seed"]] * len(jobs)))
-    for k in range(0, len(jobs), 8):
-        v, b, N = jobs[k]
-        assert got[k] == O.linear_complexity(v, b, N, c["seed"]), jobs[k]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with ThreadPoolExecutor(cores) as ex:
+        want = list(ex.map(lambda j: O.linear_complexity(j[0], j[1], j[2], c["seed"]), jobs))
+    for k, job in enumerate(jobs):
+        assert got[k] == want[k], job
     for k, (v, b, N) in enumerate(jobs):
         if b == 0 and v.endswith("+") and not v.endswith("++"):
             assert got[k] == O.state_bits(v), v

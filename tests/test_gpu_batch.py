@@ -231,18 +231,43 @@ def test_batch_large_states_alone_and_in_the_mix(ctx, xr, use_graph):
     b.close()
 
 
-def test_batch_configuration_sampled(ctx, xr):
+def oracle_requests_in_full(specs, seeds, out_np, offs, chunk=1 << 20):
+    """Every output of every request against the oracle: requests are cut into
+    chunks of `chunk` values whose start states the oracle reaches by its jump
+    polynomial (x^(k chunk) mod p), and the chunks run on every host core
+    (worker threads; the oracle's C calls release the GIL).  Returns the
+    number of values compared."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    def work(r, k0):
+        name, dt, n, _ = specs[r]
+        cnt = min(chunk, n - k0)
+        st = O.jump_pow(name, 0, k0, O.seed(name, seeds[r])) if k0 else O.seed(name, seeds[r])
+        raw, _ = O.generate(name, st, cnt)
+        es = 8 if dt in ("u64", "f64") else 4
+        got = request_view(out_np, offs[r] + k0 * es, cnt, dt)
+        assert_bits_equal(got, expected(name, raw, dt), "request %d values %d..%d" % (r, k0, k0 + cnt))
+        return cnt
+
+    tasks = [(r, k0) for r, (_, _, n, _) in enumerate(specs) for k0 in range(0, n, chunk)]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with ThreadPoolExecutor(cores) as ex:
+        return sum(ex.map(lambda t: work(*t), tasks))
+
+
+def test_batch_configuration_full(ctx, xr):
     """The batched configuration (4096 requests, lengths log-uniform up to 2^24,
-    8 generators, native/double, SplitMix64(r) seeds): every request compared
-    with the same request run alone through xr_fill_seq, the short ones and
-    sampled long ones also against the oracle."""
+    8 generators, native/double, SplitMix64(r) seeds; 30 GB) in one graph
+    launch: every request equals the same request run alone through
+    xr_fill_seq, and every value of every request equals the oracle."""
     import torch
     specs = W.batch_requests()
     seeds = [s for (_, _, _, s) in specs]
     specs = [(v, dt, n, r) for r, (v, dt, n, _) in enumerate(specs)]
     reqs, offs, arena = xr.pack_requests(specs)
     b = xr.Batch(ctx, reqs)
-    slots = torch.zeros(len(specs) * 32, dtype=torch.uint8, device="cuda")
+    slots = torch.zeros(len(specs) * b.slot_bytes, dtype=torch.uint8, device="cuda")
     out = torch.empty(arena, dtype=torch.uint8, device="cuda")
     d_seeds = torch.tensor(seeds, dtype=torch.int64, device="cuda")
     b.run(d_seeds, slots, out, use_graph=True)
@@ -255,12 +280,8 @@ def test_batch_configuration_sampled(ctx, xr):
     for r, (name, dt, n, _) in enumerate(specs):
         a, z = offs[r], offs[r] + n * xr.dtype_bytes(dt)
         assert torch.equal(out[a:z], alone[a:z]), "request %d differs from its run alone" % r
-    rng = np.random.default_rng(5)
-    check = [r for r, s in enumerate(specs) if s[2] <= 4096] + list(rng.integers(0, len(specs), 12))
+    del alone
     o = out.cpu().numpy()
-    for r in check:
-        name, dt, n, _ = specs[r]
-        raw, _ = O.generate(name, O.seed(name, seeds[r]), n)
-        assert_bits_equal(request_view(o, offs[r], n, dt), expected(name, raw, dt), "request %d" % r)
+    assert oracle_requests_in_full(specs, seeds, o, offs) == sum(n for (_, _, n, _) in specs)
     assert ctx.status() == 0
     b.close()
