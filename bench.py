@@ -275,9 +275,15 @@ def write_ceiling(xr, out, stream):
 
     store = {k: best(lambda: xr.probe_store(out, k, stream=stream)) for k in (2, 4, 8)}
     memset = best(lambda: xr.probe_memset(out, stream=stream))
+    rows, row_bytes = W.CONFIG_BULK["S"], W.CONFIG_BULK["m"] * 8
+    tiles = {name: best(lambda: xr.probe_tile_store(out, rows, row_bytes, cfg, stream=stream))
+             for cfg, name in ((0, "2 warps x 6 tiles"), (1, "1 warp x 8 tiles"), (2, "1 warp x 3 tiles"))}
     peak = max(max(store.values()), memset)
     return {"write_peak_gbs": peak, "store_kernel_gbs": store, "memset_gbs": memset, "bytes": nbytes,
-            "how": "best of 10, CUDA events on the launching stream, over the bench's 8 GiB output buffer"}
+            "tile_store_gbs": tiles,
+            "how": "best of 10, CUDA events on the launching stream, over the bench's 8 GiB output buffer; "
+                   "tile_store_gbs: the fill's own store pattern (2^20 rows of 8 KiB as 32-row x 128-byte "
+                   "TMA tiles) with nothing generated"}
 
 
 def alu_ceiling(xr, stream):
@@ -562,6 +568,8 @@ def run_xr(args):
                      "traffic_note": traffic["note"] if traffic else None,
                      "algorithmic_bytes_per_launch_u64": S * m * 8 + S * 32,
                      "write_peak_gbs": wc["write_peak_gbs"], "frac_of_write_peak": achieved / wc["write_peak_gbs"],
+                     "tile_store_ceiling_gbs": max(wc["tile_store_gbs"].values()),
+                     "frac_of_tile_store_ceiling": achieved / max(wc["tile_store_gbs"].values()),
                      "write_ceiling": wc,
                      "alu_peak_lane_ops_per_s": ac["alu_lane_ops_per_s"], "alu_ceiling": ac,
                      "jobs_alu_bound": sorted("%s/%s" % jd for jd, r in roofs.items() if r["bound"] == "alu"),

@@ -30,6 +30,16 @@ extern "C" {
  * written values are unspecified. */
 int xr_probe_store(void *d_buf, size_t bytes, int ctas_per_sm, void *stream);
 
+/* The fill's own store pattern with nothing generated: rows x row_bytes
+ * bytes at d_buf (row-major), each warp writing 32 consecutive rows as
+ * 32-row x 128-byte swizzled tiles (staged with st.shared, stored by TMA),
+ * column after column.  config 0: 2 warps per CTA x 6 tiles in flight per
+ * warp (the fill of light outputs), 1: 1 warp x 8 tiles, 2: 1 warp x 3
+ * tiles (the fill of heavy outputs).  d_buf 128-byte aligned, row_bytes a
+ * multiple of 128 (at most 2^30), rows a multiple of 32 x warps per CTA,
+ * below 2^31; else XR_EINVAL.  The written values are unspecified. */
+int xr_probe_tile_store(void *d_buf, size_t rows, size_t row_bytes, int config, void *stream);
+
 /* cudaMemsetAsync(d_buf, 0, bytes, stream): the runtime's own store path. */
 int xr_probe_memset(void *d_buf, size_t bytes, void *stream);
 

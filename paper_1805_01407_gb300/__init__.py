@@ -106,6 +106,7 @@ def lib():
             "xr_probe_store": [vp, sz, i, vp],
             "xr_probe_memset": [vp, sz, vp],
             "xr_probe_alu": [vp, i, i, vp],
+            "xr_probe_tile_store": [vp, sz, sz, i, vp],
         }
         L.xr_launch_count.argtypes = []
         L.xr_launch_count.restype = ctypes.c_uint64
@@ -201,6 +202,15 @@ def probe_store(d_buf, ctas_per_sm=0, stream=None):
     _need(d_buf, 16, "d_buf")
     _check(lib().xr_probe_store(d_buf.data_ptr(), _nbytes(d_buf) // 16 * 16, ctas_per_sm, _stream(stream)),
            "xr_probe_store")
+
+
+def probe_tile_store(d_buf, rows, row_bytes, config=0, stream=None):
+    """The fill's tile-store pattern over rows x row_bytes of d_buf, nothing
+    generated (include/xr_probe.h); config 0, 1, 2 = 2 warps x 6 tiles,
+    1 x 8, 1 x 3."""
+    _need(d_buf, rows * row_bytes, "d_buf")
+    _check(lib().xr_probe_tile_store(d_buf.data_ptr(), rows, row_bytes, config, _stream(stream)),
+           "xr_probe_tile_store")
 
 
 def probe_memset(d_buf, stream=None):

@@ -3,10 +3,13 @@
 // (independent lop3 chains) of the GPU the fill runs on.
 #include <stdint.h>
 
+#include "xr_device.cuh"
 #include "xr_internal.h"
 #include "xr_probe.h"
 
 namespace {
+
+using xr::u32;
 
 // Thread t stores the 16-byte words t, t + G, t + 2G, ... (G = grid threads):
 // each warp store covers 512 contiguous bytes.
@@ -45,6 +48,40 @@ __global__ void __launch_bounds__(256) k_probe_alu(uint32_t *sink, int trips)
     for (int j = 0; j < 8; ++j) x ^= a[j] * (2u * j + 1u);
     // a store that depends on every chain and practically never happens
     if (x == 0x2545f491u) *sink = x;
+}
+
+// The fill's tile-store pattern with nothing generated: each warp owns 32
+// consecutive rows and writes them as 32-row x 128-byte swizzled tiles, column
+// after column, staging each tile with st.shared first, NBUF tiles in flight
+// per warp; one warp per 32 rows over the grid.  Coordinates stay inside the
+// tensor: x below the row length in steps of 16 u64, row0 below `rows` (the
+// grid is rows / (32 WARPS)).
+template <int WARPS, int NBUF>
+__global__ void __launch_bounds__(WARPS * 32) k_probe_tiles(const __grid_constant__ CUtensorMap map, int cols)
+{
+    extern __shared__ unsigned char probe_smem[];
+    const u32 base = (xr::smem_addr(probe_smem) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = (blockIdx.x * WARPS + warp) * 32;
+    const u32 tiles = base + (u32)(warp * NBUF * 4096);
+    int it = 0;
+    for (int j0 = 0; j0 < cols; j0 += 16, ++it) {
+        const u32 tile = tiles + (u32)((it % NBUF) * 4096);
+        if (it >= NBUF) {
+            if (lane == 0) xr::bulk_wait_read<NBUF - 1>();
+            __syncwarp();
+        }
+        const u32 row = tile + (u32)lane * 128u, sw = (u32)(lane & 7);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) xr::st_shared_v4(row + (((u32)c ^ sw) << 4), (u32)j0, (u32)c, (u32)lane, (u32)it);
+        xr::fence_proxy_async_shared();
+        __syncwarp();
+        if (lane == 0) {
+            xr::tma_store_2d(&map, tile, j0, row0);
+            xr::bulk_commit();
+        }
+    }
+    if (lane == 0) xr::bulk_wait_read<0>();
 }
 
 int status_of(cudaError_t e)
@@ -90,4 +127,50 @@ extern "C" int xr_probe_alu(uint32_t *d_sink, int blocks, int iters, void *strea
     k_probe_alu<<<blocks, 256, 0, (cudaStream_t)stream>>>(d_sink, iters / 8);
     xr::count_launch();
     return status_of(cudaGetLastError());
+}
+
+template <int WARPS, int NBUF>
+static int probe_tiles(const CUtensorMap &map, size_t rows, int cols, cudaStream_t st)
+{
+    const int smem = WARPS * NBUF * 4096 + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_probe_tiles<WARPS, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return status_of(e);
+    k_probe_tiles<WARPS, NBUF><<<(unsigned)(rows / (32 * WARPS)), WARPS * 32, smem, st>>>(map, cols);
+    xr::count_launch();
+    return status_of(cudaGetLastError());
+}
+
+extern "C" int xr_probe_tile_store(void *d_buf, size_t rows, size_t row_bytes, int config, void *stream)
+{
+    static const int warps_of[3] = {2, 1, 1};
+    if (!d_buf || ((uintptr_t)d_buf % 128) || config < 0 || config > 2 || row_bytes == 0 || (row_bytes % 128) ||
+        row_bytes > ((size_t)1 << 30) || rows == 0 || rows >= ((size_t)1 << 31) ||
+        (rows % (32 * (size_t)warps_of[config])))
+        return XR_EINVAL;
+    static xr::EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return XR_ECUDA;
+        encode = (xr::EncodeTiledFn)fn;
+    }
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)(row_bytes / 8), (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+    const cuuint32_t box[2] = {16u, 32u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, d_buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return XR_EINVAL;
+    const int cols = (int)(row_bytes / 8);
+    const cudaStream_t st = (cudaStream_t)stream;
+    switch (config) {
+    case 0: return probe_tiles<2, 6>(map, rows, cols, st);
+    case 1: return probe_tiles<1, 8>(map, rows, cols, st);
+    default: return probe_tiles<1, 3>(map, rows, cols, st);
+    }
 }
