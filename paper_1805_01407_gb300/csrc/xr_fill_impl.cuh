@@ -25,25 +25,43 @@ constexpr int TILE_BYTES = 32 * 128;   // 32 rows x 128 bytes
 constexpr int FILL_SMEM = FILL_WARPS * FILL_NBUF * TILE_BYTES + 1024;  // + alignment slack
 
 // Tile-store path: warps per CTA and tiles in flight per warp, by how much
-// integer work a byte costs.  Measured on GB300 over {1,2,4} warps x {2..8}
-// tiles: outputs that leave the ALU idle (native words, and doubles of 32-bit
-// generators) gain from more tiles per warp in flight behind the TMA unit (6
-// per warp, 2 warps per CTA), while the heavier ones need the warps instead:
-// 4 tiles x 2 warps for the exact doubles of 128-bit states, 3 tiles x 1 warp
-// (the most CTAs per SM) for the doubles of 256-bit and larger states and for
-// every output of xoshiro512 (whose 8-word step is the costliest; the 16-word
-// xoroshiro1024 step touches only 3 words).
+// integer work a byte costs.  The store pattern alone (nothing generated)
+// reaches 7.49 TB/s with 1 warp x 8 tiles, 7.35 with 2 x 6 and 7.02 with 1 x
+// 3; with the generation included, measured on GB300 per output class:
+//   - native words without a multiplying scrambler, and every output of the
+//     32-bit generators, leave the ALU and FMA pipes idle enough for the
+//     deepest queue: 8 tiles x 1 warp;
+//   - native words of the 64-bit * and ** generators need the warps: 6 tiles
+//     x 2 warps (1 x 8 measured 3 % slower for xoshiro256**);
+//   - the exact doubles of the 64-bit + generators: 6 tiles x 1 warp (2-3 %
+//     faster than the classes below, which were 3-11 % slower with it for
+//     ++ and **);
+//   - the other exact doubles of 128-bit states: 4 tiles x 2 warps; of
+//     256-bit states, and every output of xoshiro512 (whose 8-word step is the
+//     costliest; the 16-word xoroshiro1024 step touches only 3 words): 3 tiles
+//     x 1 warp, the most CTAs per SM.
 // Short rows (at most FILL_SHORT_TILES tiles, so a warp lives only a few
 // tiles) take 4 warps x 2 tiles instead: there the warps per SM count, not the
 // depth of the store queue.
 constexpr int FILL_SHORT_TILES = 4;
 
+// Generators whose scrambler multiplies (* and **), and whose scrambler is +.
+constexpr bool fill_mul_scrambler(int v)
+{
+    return v == 2 || v == 5 || v == 7 || v == 9 || v == 10 || v == 11 || v == 14 || v == 15 || v == 17;
+}
+constexpr bool fill_plus_scrambler(int v) { return v == 0 || v == 3 || v == 8 || v == 12; }
+
 template <int V, int DT, bool SHORT>
 struct FillCfg {
-    static constexpr bool f64w = DT == DT_F64 && sizeof(typename Gen<V>::word) == 8;
-    static constexpr bool heavy = (f64w && Gen<V>::E::NBITS >= 256) || Gen<V>::E::NBITS == 512;
-    static constexpr int WARPS = SHORT ? 4 : heavy ? 1 : 2;
-    static constexpr int NBUF = SHORT ? 2 : heavy ? 3 : (f64w ? 4 : 6);
+    static constexpr bool word64 = sizeof(typename Gen<V>::word) == 8;
+    static constexpr bool f64w = DT == DT_F64 && word64;
+    static constexpr bool e512 = Gen<V>::E::NBITS == 512;
+    static constexpr bool heavy = (f64w && Gen<V>::E::NBITS >= 256) || e512;
+    static constexpr bool deep = !e512 && !f64w && !(word64 && fill_mul_scrambler(V));
+    static constexpr bool plus_f64 = !e512 && f64w && fill_plus_scrambler(V);
+    static constexpr int WARPS = SHORT ? 4 : (deep || plus_f64 || heavy) ? 1 : 2;
+    static constexpr int NBUF = SHORT ? 2 : deep ? 8 : plus_f64 ? 6 : heavy ? 3 : (f64w ? 4 : 6);
     static constexpr int SMEM = WARPS * NBUF * TILE_BYTES + 1024;
 };
 
