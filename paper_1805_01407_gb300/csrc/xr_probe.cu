@@ -147,16 +147,17 @@ extern "C" int xr_probe_tile_store(void *d_buf, size_t rows, size_t row_bytes, i
         row_bytes > ((size_t)1 << 30) || rows == 0 || rows >= ((size_t)1 << 31) ||
         (rows % (32 * (size_t)warps_of[config])))
         return XR_EINVAL;
-    static xr::EncodeTiledFn encode = nullptr;
-    if (!encode) {
+    // looked up once, thread-safely (a function-local static)
+    static const xr::EncodeTiledFn encode = [] {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
             q != cudaDriverEntryPointSuccess)
-            return XR_ECUDA;
-        encode = (xr::EncodeTiledFn)fn;
-    }
+            return (xr::EncodeTiledFn) nullptr;
+        return (xr::EncodeTiledFn)fn;
+    }();
+    if (!encode) return XR_ECUDA;
     CUtensorMap map;
     const cuuint64_t dims[2] = {(cuuint64_t)(row_bytes / 8), (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
