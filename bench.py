@@ -93,7 +93,7 @@ def jobs():
 
 
 def dtype_bytes(d):
-    return 8 if d in ("u64", "f64") else 4
+    return 8 if d in ("u64", "f64") else 4  # u32, f32
 
 
 def state_bytes(v):
@@ -595,6 +595,8 @@ def run_xr(args):
             line["extra_generators"]["cpu_baseline"] = extra_cpu_baseline()
     if not args.no_jumpstart:
         line["jumpstart"] = run_jumpstart(xr, ctx, args, wc, ac)
+    if not args.no_extra:
+        line["layouts_and_types"] = run_layouts(xr, ctx, wc)
     if not args.no_analysis:
         line["analysis"] = run_analysis(xr, ctx, args)
     if not args.no_e2e:
@@ -709,6 +711,45 @@ def run_extra(xr, ctx, args, wc, ac):
                                      "alu_bound_gbs": r["alu_bound_gbs"],
                                      "frac_of_roofline": gbs / r["roofline_gbs"]}
             del out
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    return res
+
+
+def run_layouts(xr, ctx, wc):
+    """The other output forms at the bulk size (2^20 streams x 2^10 values,
+    SplitMix64(42) base, jump-started): the interleaved layout out[j S + i]
+    (coalesced warp stores, no staging) beside stream-major, and float32
+    outputs (upper 24 bits), with the 32-bit generator the paper recommends
+    for floats (xoshiro128+) and a 64-bit one; fill alone, median of 5,
+    events on the stream, against the measured write peak."""
+    import torch
+    S, m, seed = W.CONFIG_BULK["S"], W.CONFIG_BULK["m"], W.CONFIG_BULK["seed"]
+    stream = torch.cuda.current_stream()
+    res = {}
+    for v, d, layout in (("xoshiro256**", "u64", "stream"), ("xoshiro256**", "u64", "interleaved"),
+                         ("xoshiro256**", "f64", "interleaved"), ("xoshiro128+", "f32", "stream"),
+                         ("xoshiro128+", "f32", "interleaved"), ("xoshiro256+", "f32", "stream")):
+        base = ctx.empty_states(v, 1)
+        states = ctx.empty_states(v, S)
+        ctx.seed(v, seed, base)
+        ctx.make_streams(v, "jump", base, 0, S, states)
+        out = ctx.empty_output(S * m, d)
+        for _ in range(2):
+            ctx.fill(v, states, S, m, d, out, layout=layout)
+        ts = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.fill(v, states, S, m, d, out, layout=layout)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        gbs = S * m * dtype_bytes(d) / (ms / 1e3) / 1e9
+        res["%s/%s/%s" % (v, d, layout)] = {"fill_ms": ms, "fill_gbs": gbs,
+                                            "frac_of_write_peak": gbs / wc["write_peak_gbs"]}
+        del out, states
     torch.cuda.synchronize()
     assert ctx.status() == 0
     return res

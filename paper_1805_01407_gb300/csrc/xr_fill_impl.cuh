@@ -268,8 +268,31 @@ __global__ void __launch_bounds__(256)
     E e;
     load_state(e, (const char *)states + i * sizeof(e.s));
     if (state_is_zero(e)) atomicCAS(status, 0, XR_EZERO_STATE);
+    size_t j = 0;
+    if constexpr (DT == DT_F64 && sizeof(typename G::word) == 8 && E::NBITS <= 512) {
+        // doubles of 64-bit words in chunks of 16 with the branch-free
+        // conversion; a chunk holding an output below 2^32 (probability 2^-28
+        // per chunk) is written again exactly from its start state
+        for (; j + 16 <= m; j += 16) {
+            const E e0 = e;
+            u32 hmin = 0xffffffffu;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                out[(j + q) * S + i] = unit_f64_bits_hi((u64)G::out(e), hmin);
+                e.step();
+            }
+            if (__builtin_expect(hmin == 0u, 0)) {
+                E r = e0;
+#pragma unroll 1
+                for (int q = 0; q < 16; ++q) {
+                    out[(j + q) * S + i] = unit_f64_bits((u64)G::out(r));
+                    r.step();
+                }
+            }
+        }
+    }
 #pragma unroll 4
-    for (size_t j = 0; j < m; ++j) {
+    for (; j < m; ++j) {
         out[j * S + i] = convert<DT>(G::out(e));
         e.step();
     }
