@@ -308,6 +308,37 @@ def test_fill_seq(ctx, xr, name):
             assert (states_from_device(name, d_state)[0] == after).all()
 
 
+@pytest.mark.parametrize("name,dtype", [("xoshiro256**", "u64"), ("xoroshiro128++", "f64"), ("xoshiro128+", "u32")])
+def test_fill_seq_long_full(ctx, xr, name, dtype):
+    """One sequence of 2^28 + 5000 values (2^18 + 5 segments of 2^10, so the
+    segment starts use all three power-set levels and a ragged tail), with
+    canaries, every value against the oracle: chunks of 2^20 values started
+    by the oracle's own jump polynomial (x^(k 2^20) mod p), on every host core;
+    and the state advanced by n."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    n, chunk = (1 << 28) + 5000, 1 << 20
+    s0 = O.seed(name, 4242)
+    d_state = states_to_device(name, s0[None, :])
+    buf, view, start, nb = guarded_output(xr, n, dtype)
+    ctx.fill_seq(name, d_state, n, dtype, as_dtype(view, dtype))
+    torch.cuda.synchronize()
+    check_canaries(buf, start, nb)
+    got = out_to_numpy(as_dtype(view, dtype), dtype)
+    assert (states_from_device(name, d_state)[0] == O.jump_pow(name, 0, n, s0)).all()
+
+    def work(k0):
+        cnt = min(chunk, n - k0)
+        raw, _ = O.generate(name, O.jump_pow(name, 0, k0, s0) if k0 else s0, cnt)
+        assert_bits_equal(got[k0:k0 + cnt], expected(name, raw, dtype), "%s values %d.." % (name, k0))
+        return cnt
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with ThreadPoolExecutor(cores) as ex:
+        assert sum(ex.map(work, range(0, n, chunk))) == n
+    assert ctx.status() == 0
+
+
 # ------------------------------------------------------------------ configurations
 
 def test_plain_configuration_full(ctx, xr):
