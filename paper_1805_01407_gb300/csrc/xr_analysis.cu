@@ -134,119 +134,204 @@ __global__ void __launch_bounds__(128) k_lc_bits(const u32 *__restrict__ tables,
     }
 }
 
-// One CTA per job, everything in registers.  Thread t holds words t R ..
-// t R + R - 1 of three bit strings:
-//   c   = C, the connection polynomial;
-//   xb  = x^m B, B being C before the last length change;
-//   win = the window, bit i = s_{n-i} (zero for i > n).
-// Step n (d_n known): C_{n+1} = C_n + d_n x^m B; x^m B moves to x^(m+1) B, or
-// to x C_n when the length changes (B = C_n, m = 1); the window moves up one
-// bit and takes s_{n+1} at bit 0.  Each is a shift by one bit, so a word only
-// needs the top word of the word below it: from the lane below by shuffle, or
-// for lane 0 from the previous warp's lane 31, which publishes its top words
-// in shared memory before every barrier.  Then d_{n+1} = parity(c & win).
+// One CTA per job, blocked Berlekamp-Massey: a barrier per block of (up to)
+// 32 sequence bits instead of one per bit.  Notation of the bit-serial
+// algorithm: C_n the connection polynomial, L_n its length, and
+// X_n = x^m B, B being C before the last length change; step n with
+// discrepancy d_n = sum_t C_t s_{n-t} sets C_{n+1} = C_n + d_n X_n and
+// X_{n+1} = x C_n when the length changes (d_n = 1 and 2 L_n <= n, then
+// L_{n+1} = n + 1 - L_n), else x X_n.  Over one block n .. n+k-1 every
+// C_{n+u} is a C_n + b X_n with polynomials a, b of degree <= u, so each
+// d_{n+u} follows from the 2k lookahead parities
+//   e_C(u) = sum_t (C_n)_t s_{n+u-t},   e_X(u) = sum_t (X_n)_t s_{n+u-t}:
+//   d_{n+u} = sum_j a_j e_C(u-j) + b_j e_X(u-j).
+// A block is then:
+//   1. lookahead: each thread ANDs its words of C_n and X_n with the 32
+//      windows s_{n+u-32w-31 .. n+u-32w}, read straight from the packed
+//      reversed sequence (one funnel shift per word and u), and folds the
+//      parities into two 32-bit masks; a warp XORs its lanes' masks by
+//      shuffles, and the warps' masks meet in shared memory at the block's
+//      first barrier;
+//   2. the k steps on the 2x2 polynomial matrix, by warp 0 alone (scalar,
+//      branch-free): the steps with d = 1 and the length changes as two bit
+//      masks, and the new L, go to shared memory; a second barrier publishes
+//      them;
+//   3. replay on the words, visiting only the steps with d = 1.  X is held
+//      lazily as x^(u - tau) Y (Y = X_n at first, Y = C_{n+tau} after a
+//      length change at step tau), so such a step costs one funnel shift and
+//      one XOR per word, and the block ends with one shift of Y.
+// Thread t holds words tR .. tR+R-1 of C and Y.  A shift brings in bits of
+// the word below, owned by the lane below or by the previous warp's lane 31.
+// Instead of exchanging them every step, a thread replays a shadow of that
+// word from its value at the block's start (by shuffle, or from shared memory
+// written at the end of the previous block) with zeros shifted in below: after
+// shifts totalling u bits only its lowest u bits can be wrong, and a shift
+// that ends at step u <= 32 reads only bits at or above u, so a block of
+// k <= 32 steps needs no exchange.
 //
-// deg C <= L, deg x^m B <= n + 2 and deg win <= n + 1 after step n, so a
-// thread whose first word is above (n + 2) / 32 + 1 holds zeros and skips the
-// step.  Bits shifted past the last word are never needed: an update uses
-// x^m B only when its degree is below the new L, which is checked against
-// 32 W first (a larger complexity stores ~0 instead of a result).
+// deg C_n <= L_n and deg X_n <= n + 1 - L_n, so words above
+// max(L, n+1-L) / 32 are zero at the block's start (no lookahead) and stay
+// zero above (max + 32) / 32 through the block (no replay).  Bits shifted
+// past the last word are never needed: X is added to C only when its degree
+// is below the new L, which is checked against 32 W first (a larger
+// complexity stores ~0 instead of a result).
 //
-// One barrier per sequence bit, which also reduces the parity: d_{n+1} is
-// the parity of the number of threads whose partial sum is odd
-// (__syncthreads_count).  The carry slots alternate, so a slot is rewritten
-// two barriers after it was read.
+// Blocks end on sequence positions N - 32 j, so each block's windows start on
+// a word boundary of the packed reversed sequence (bit i of rev = s_{N-1-i});
+// the first block takes the remaining ((N - 1) mod 32) + 1 steps.
+template <int R, bool FULL>
+__device__ __forceinline__ void bm_lookahead(const u32 *__restrict__ rev, u32 k, const u32 (&c)[R],
+                                             const u32 (&y)[R], u32 &eC, u32 &eX)
+{
+    u32 rv[R + 1];
+#pragma unroll
+    for (int i = 0; i <= R; ++i) rv[i] = __ldg(rev + i);
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+        if (!FULL && (u32)u >= k) break;
+        const u32 s = FULL ? (u32)(31 - u) : k - 1 - (u32)u;
+        u32 ac = 0u, ax = 0u;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const u32 t = __funnelshift_r(rv[j], rv[j + 1], s);  // window word j at step n + u
+            ac ^= c[j] & t;
+            ax ^= y[j] & t;
+        }
+        eC |= (u32)(__popc(ac) & 1) << u;
+        eX |= (u32)(__popc(ax) & 1) << u;
+    }
+}
+
 template <int R>
 __global__ void __launch_bounds__(1024) k_berlekamp_massey(const LcJob *__restrict__ jobs)
 {
-    __shared__ uint4 carry[2][32];  // [slot][warp]: top words of c, xb, win
+    __shared__ uint2 masks[2][32];  // [slot][warp]: the warp's e_C, e_X masks
+    __shared__ uint2 tops[2][32];   // [slot][warp]: top words of C, Y of the warp's lane 31
+    __shared__ uint4 steps[2];      // [slot]: d mask, length-change mask, L, overflow
     const LcJob job = jobs[blockIdx.x];
     const u32 N = job.N, W = job.W;
-    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    const u32 *rev = job.rev;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const u32 w0 = (u32)tid * R;
-    for (int i = tid; i < 2 * 32; i += nth) (&carry[0][0])[i] = make_uint4(0u, 0u, 0u, 0u);
-    u32 c[R], xb[R], win[R];
+    for (int i = tid; i < 2 * 32; i += blockDim.x) (&tops[0][0])[i] = make_uint2(0u, 0u);
+    u32 c[R], y[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) c[k] = xb[k] = win[k] = 0u;
-    // bit j of the packed sequence is s_{N-1-j}
-    const u32 s0 = (__ldg(rev + ((N - 1) >> 5)) >> ((N - 1) & 31)) & 1u;
+    for (int j = 0; j < R; ++j) c[j] = y[j] = 0u;
     if (tid == 0) {
-        c[0] = 1u;   // C = 1
-        xb[0] = 2u;  // x^1 B, B = 1
-        win[0] = s0;
+        c[0] = 1u;  // C = 1
+        y[0] = 2u;  // X = x^1 B, B = 1
     }
-    int d = (int)s0;
-    u32 sword = 0u;  // thread 0: the packed word holding s_{n+1}
-    u32 L = 0;
+    u32 L = 0, n = 0;
+    int slot = 0;
     __syncthreads();
-    for (u32 n = 0; n < N; ++n) {
-        const bool grow = d && 2 * L <= n;
-        const u32 Lnew = grow ? n + 1 - L : L;
-        if (d && Lnew >= W * 32) {  // uniform
+    while (n < N) {
+        const u32 k = ((N - 1 - n) & 31u) + 1u;
+        const u32 q = (N - 1 - n - (k - 1)) >> 5;  // rev word of window word 0 at step n + k - 1
+        const u32 D = L > n + 1 - L ? L : n + 1 - L;
+        u32 eC = 0u, eX = 0u;
+        if (w0 <= D / 32) {
+            if (k == 32) bm_lookahead<R, true>(job.rev + q + w0, k, c, y, eC, eX);
+            else bm_lookahead<R, false>(job.rev + q + w0, k, c, y, eC, eX);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            eC ^= __shfl_xor_sync(0xffffffffu, eC, o);
+            eX ^= __shfl_xor_sync(0xffffffffu, eX, o);
+        }
+        u32 sC = __shfl_up_sync(0xffffffffu, c[R - 1], 1);
+        u32 sY = __shfl_up_sync(0xffffffffu, y[R - 1], 1);
+        if (lane == 0) masks[slot][warp] = make_uint2(eC, eX);
+        __syncthreads();
+        if (lane == 0) {
+            if (warp == 0) {
+                sC = sY = 0u;
+            } else {
+                const uint2 t = tops[slot][warp - 1];
+                sC = t.x;
+                sY = t.y;
+            }
+        }
+        if (warp == 0) {
+            eC = eX = 0u;
+            for (int w = 0; w < nwarps; ++w) {
+                const uint2 t = masks[slot][w];
+                eC ^= t.x;
+                eX ^= t.y;
+            }
+            // a, b (C_{n+u} = a C_n + b X_n) and a', b' (X_{n+u} = a' C_n +
+            // b' X_n), each aligned to bit 31 - u, so that with E = brev(e)
+            // (bit 31 - v = e(v)) the discrepancy is parity((A & E_C) ^ (B & E_X)).
+            const u32 EC = __brev(eC), EX = __brev(eX);
+            u32 A = 0x80000000u, B = 0u, A2 = 0u, B2 = 0x80000000u, dm = 0u, gm = 0u, over = 0u;
+            for (u32 u = 0; u < k; ++u) {
+                const u32 dmask = 0u - (u32)(__popc((A & EC) ^ (B & EX)) & 1);
+                const u32 gmask = dmask & (0u - (u32)(2 * L <= n + u));
+                const u32 Lg = n + u + 1 - L;
+                over |= gmask & (0u - (u32)(Lg >= W * 32));
+                const u32 nA = A ^ (A2 & dmask), nB = B ^ (B2 & dmask);
+                A2 = (A & gmask) | (A2 & ~gmask);
+                B2 = (B & gmask) | (B2 & ~gmask);
+                A = nA >> 1;
+                B = nB >> 1;
+                L = gmask ? Lg : L;
+                dm |= (dmask & 1u) << u;
+                gm |= (gmask & 1u) << u;
+            }
+            if (lane == 0) steps[slot] = make_uint4(dm, gm, L, over);
+        }
+        __syncthreads();
+        const uint4 sd = steps[slot];
+        if (sd.w) {  // uniform
             if (tid == 0) *job.out = ~0ull;
             return;
         }
-        const int slot = (int)(n & 1);
-        u32 cc = __shfl_up_sync(0xffffffffu, c[R - 1], 1);
-        u32 cx = __shfl_up_sync(0xffffffffu, xb[R - 1], 1);
-        u32 cw = __shfl_up_sync(0xffffffffu, win[R - 1], 1);
-        if (lane == 0) {
-            if (warp == 0) {
-                cc = cx = cw = 0u;
-                if (n + 1 < N) {
-                    const u32 j = N - 2 - n;
-                    if (n == 0 || (j & 31) == 31) sword = __ldg(rev + (j >> 5));
-                    cw = ((sword >> (j & 31)) & 1u) << 31;
+        L = sd.z;
+        if (w0 <= (D + 32) / 32) {
+            u32 ev = sd.x, tau = 0u;
+            while (ev) {
+                const u32 u = (u32)__ffs(ev) - 1u;
+                ev &= ev - 1u;
+                const u32 dl = u - tau;  // X_{n+u} = x^dl Y, dl < 32
+                const u32 sx = sY << dl;
+                if ((sd.y >> u) & 1u) {  // length change: Y = C_{n+u}, tau = u
+#pragma unroll
+                    for (int j = R - 1; j >= 0; --j) {
+                        const u32 xw = __funnelshift_l(j ? y[j - 1] : sY, y[j], dl);
+                        y[j] = c[j];
+                        c[j] ^= xw;
+                    }
+                    const u32 t = sC;
+                    sC ^= sx;
+                    sY = t;
+                    tau = u;
+                } else {
+#pragma unroll
+                    for (int j = R - 1; j >= 0; --j) c[j] ^= __funnelshift_l(j ? y[j - 1] : sY, y[j], dl);
+                    sC ^= sx;
                 }
-            } else {
-                const uint4 t = carry[slot][warp - 1];
-                cc = t.x;
-                cx = t.y;
-                cw = t.z;
             }
+            const u32 sh = k - tau;  // X_{n+k} = x^sh Y, 1 <= sh <= 32
+#pragma unroll
+            for (int j = R - 1; j >= 0; --j) y[j] = __funnelshift_lc(j ? y[j - 1] : sY, y[j], sh);
         }
-        u32 acc = 0u;
-        if (w0 <= (n + 2) / 32 + 1) {
-            if (grow) {
-#pragma unroll
-                for (int k = R - 1; k >= 0; --k) {
-                    const u32 nx = __funnelshift_l(k ? c[k - 1] : cc, c[k], 1);
-                    c[k] ^= xb[k];
-                    xb[k] = nx;
-                }
-            } else if (d) {
-#pragma unroll
-                for (int k = R - 1; k >= 0; --k) {
-                    c[k] ^= xb[k];
-                    xb[k] = __funnelshift_l(k ? xb[k - 1] : cx, xb[k], 1);
-                }
-            } else {
-#pragma unroll
-                for (int k = R - 1; k >= 0; --k) xb[k] = __funnelshift_l(k ? xb[k - 1] : cx, xb[k], 1);
-            }
-#pragma unroll
-            for (int k = R - 1; k >= 0; --k) {
-                win[k] = __funnelshift_l(k ? win[k - 1] : cw, win[k], 1);
-                acc ^= c[k] & win[k];
-            }
-        }
-        L = Lnew;
-        if (lane == 31) carry[slot ^ 1][warp] = make_uint4(c[R - 1], xb[R - 1], win[R - 1], 0u);
-        d = __syncthreads_count((int)(__popc(acc) & 1)) & 1;
+        n += k;
+        if (lane == 31) tops[slot ^ 1][warp] = make_uint2(c[R - 1], y[R - 1]);
+        slot ^= 1;
     }
     if (tid == 0) *job.out = (unsigned long long)L;
 }
 
-// Words per thread: 12 (measured best on GB300 from one to 448 sequences of
-// 2^16 to 7 10^5 bits: enough words per warp to outweigh the per-step
-// shuffles, carry exchange and barrier, few enough registers for 1024
-// threads), or the fewest that fit one warp for sequences under 12 288 bits.
-static int lc_r(u32 W)
+// Words per thread (at most 1024 threads per sequence): the fewest of 1, 2,
+// 4, 8 that fit one warp; otherwise 8 when at least one sequence per SM is
+// running (448 sequences of 2^16 bits: R = 4, 8, 12 took 12.0, 11.9, 12.5 ms
+// on GB300), and 4 for fewer sequences, which then have an SM each (one
+// 65,992-bit sequence: 6.7, 7.8, 8.6 ms); 12 where 8 does not fit (above
+// about 524,000 bits).
+static int lc_r(u32 W, bool many)
 {
     for (int r : {1, 2, 4, 8})
         if ((W + r - 1) / r <= 32) return r;
-    return 12;
+    if (!many && (W + 3) / 4 <= 1024) return 4;
+    return (W + 7) / 8 <= 1024 ? 8 : 12;
 }
 
 template <int R>
@@ -338,10 +423,13 @@ static int lc_run(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, const void *
     }
     // jobs ordered by (words per thread, variant): one Berlekamp-Massey launch
     // per words-per-thread group, one bit-generation launch per variant run
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) return XR_ECUDA;
+    const bool many = njobs >= (size_t)sms;
     std::vector<size_t> order(njobs);
     for (size_t j = 0; j < njobs; ++j) order[j] = j;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
-        const int ra = lc_r(lc_words(jobs[a].N)), rb = lc_r(lc_words(jobs[b].N));
+        const int ra = lc_r(lc_words(jobs[a].N), many), rb = lc_r(lc_words(jobs[b].N), many);
         return ra != rb ? ra < rb : jobs[a].variant < jobs[b].variant;
     });
     char *base = (char *)d_scratch;
@@ -375,7 +463,7 @@ static int lc_run(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, const void *
     for (size_t i = 0; err == cudaSuccess && i < njobs;) {  // one launch per variant run
         size_t e = i, max_threads = 0;
         while (e < njobs && jobs[order[e]].variant == jobs[order[i]].variant &&
-               lc_r(h_jobs[e].W) == lc_r(h_jobs[i].W)) {
+               lc_r(h_jobs[e].W, many) == lc_r(h_jobs[i].W, many)) {
             max_threads = std::max(max_threads, ((size_t)h_jobs[e].N + h_jobs[e].chunk - 1) / h_jobs[e].chunk);
             ++e;
         }
@@ -384,10 +472,10 @@ static int lc_run(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, const void *
         i = e;
     }
     for (size_t i = 0; err == cudaSuccess && i < njobs;) {  // one launch per words-per-thread group
-        const int R = lc_r(h_jobs[i].W);
+        const int R = lc_r(h_jobs[i].W, many);
         size_t e = i;
         u32 Wmax = 0;
-        while (e < njobs && lc_r(h_jobs[e].W) == R) {
+        while (e < njobs && lc_r(h_jobs[e].W, many) == R) {
             Wmax = std::max(Wmax, h_jobs[e].W);
             ++e;
         }
