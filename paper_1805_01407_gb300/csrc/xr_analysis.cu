@@ -354,6 +354,313 @@ static cudaError_t launch_bm(int R, const LcJob *d_jobs, unsigned count, u32 Wma
     }
 }
 
+// ---------------------------------------------------------------- one sequence on a cluster of CTAs
+//
+// The same blocked algorithm for calls with few sequences, which would leave
+// most SMs idle with one CTA each: a cluster of LC_CLUSTER CTAs (one per SM)
+// shares a sequence, global thread g = rank * blockDim + tid holding words
+// gR .. gR+R-1.  Per block, every warp sends its lookahead masks to every
+// CTA of the cluster with st.async, which lands them in that CTA's shared
+// memory and counts their bytes on its mbarrier; the CTA before this one sends
+// its last thread's top words (the shadow of this CTA's first thread) the same
+// way.  Only warp 0 of each CTA waits, on its own mbarrier, then runs the
+// block recurrence; all CTAs see the same masks, so they take the same
+// decisions and exit on overflow at the same block.  A CTA sends block b + 2's
+// masks only after receiving everyone's block b + 1 masks, which each CTA
+// sent after reading its block b masks, so two slots suffice and an mbarrier
+// phase never receives bytes of the next one.  Cluster barriers come only
+// before the first remote store (every mbarrier initialised) and before exit
+// (no CTA leaves while another may still store into it).  A wait that runs out
+// (LC_WAIT_TRIES polls) makes its CTA report ~1, which the call turns into an
+// error, and return.
+constexpr unsigned LC_CLUSTER = 8;
+
+__device__ __forceinline__ u32 cluster_ctarank()
+{
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ u32 cluster_nctarank()
+{
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// v into the same shared-memory variable of CTA `rank` of the cluster
+__device__ __forceinline__ void st_cluster(const uint2 *local, u32 rank, uint2 v)
+{
+    const u32 a = (u32)__cvta_generic_to_shared(local);
+    u32 ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("st.shared::cluster.v2.u32 [%0], {%1, %2};" ::"r"(ra), "r"(v.x), "r"(v.y) : "memory");
+}
+
+__device__ __forceinline__ u32 smem_addr32(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ u32 mapa32(u32 a, u32 rank)
+{
+    u32 r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+// 8 bytes into shared memory of another CTA of the cluster, counted on that
+// CTA's mbarrier (transaction bytes)
+__device__ __forceinline__ void st_async8(u32 raddr, uint2 v, u32 rmbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.u32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+                 "r"(v.x), "r"(v.y), "r"(rmbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(u32 a, u32 count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(u32 a, u32 bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ u32 mbar_try_wait(u32 a, u32 parity)
+{
+    u32 ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok;
+}
+
+constexpr u32 LC_WAIT_TRIES = 1u << 24;
+
+template <int R>
+__global__ void __launch_bounds__(1024) k_berlekamp_massey_cluster(const LcJob *__restrict__ jobs)
+{
+    __shared__ uint2 parts[2][LC_CLUSTER * 32];  // [slot][rank * nwarps + warp]: every warp's e_C, e_X
+    __shared__ uint2 tops[2][32];                // [slot][warp]: top words of C, Y of the warp's lane 31
+    __shared__ uint2 ctop[2];                    // [slot]: top words of the previous CTA's last thread
+    __shared__ uint4 steps[2];                   // [slot]: d mask, length-change mask, L, overflow / timeout
+    __shared__ __align__(8) unsigned long long mbar[2];  // [slot]: parts and ctop of the block arrived
+    const u32 rank = cluster_ctarank(), ncta = cluster_nctarank();
+    const LcJob job = jobs[blockIdx.x / ncta];
+    const u32 N = job.N, W = job.W;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const u32 g = rank * blockDim.x + (u32)tid, w0 = g * R;
+    for (int i = tid; i < 2 * 32; i += blockDim.x) (&tops[0][0])[i] = make_uint2(0u, 0u);
+    if (tid < 2) ctop[tid] = make_uint2(0u, 0u);
+    if (tid == 0) {
+        mbar_init(smem_addr32(&mbar[0]), 1);
+        mbar_init(smem_addr32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    u32 c[R], y[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) c[j] = y[j] = 0u;
+    if (g == 0) {
+        c[0] = 1u;
+        y[0] = 2u;
+    }
+    u32 L = 0, n = 0, parity = 0u;  // parity: bit s = phase parity of mbar[s]
+    int slot = 0;
+    const u32 tx = ncta * (u32)nwarps * 8u + (rank ? 8u : 0u);
+    cluster_barrier();  // every CTA initialised before the first remote store
+    while (n < N) {
+        const u32 k = ((N - 1 - n) & 31u) + 1u;
+        const u32 q = (N - 1 - n - (k - 1)) >> 5;
+        const u32 D = L > n + 1 - L ? L : n + 1 - L;
+        u32 eC = 0u, eX = 0u;
+        if (w0 <= D / 32) {
+            if (k == 32) bm_lookahead<R, true>(job.rev + q + w0, k, c, y, eC, eX);
+            else bm_lookahead<R, false>(job.rev + q + w0, k, c, y, eC, eX);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            eC ^= __shfl_xor_sync(0xffffffffu, eC, o);
+            eX ^= __shfl_xor_sync(0xffffffffu, eX, o);
+        }
+        u32 sC = __shfl_up_sync(0xffffffffu, c[R - 1], 1);
+        u32 sY = __shfl_up_sync(0xffffffffu, y[R - 1], 1);
+        const u32 mb = smem_addr32(&mbar[slot]);
+        if ((u32)lane < ncta)
+            st_async8(mapa32(smem_addr32(&parts[slot][rank * nwarps + warp]), (u32)lane), make_uint2(eC, eX),
+                      mapa32(mb, (u32)lane));
+        if (tid == (int)blockDim.x - 1 && rank + 1 < ncta)
+            st_async8(mapa32(smem_addr32(&ctop[slot]), rank + 1), make_uint2(c[R - 1], y[R - 1]), mapa32(mb, rank + 1));
+        if (warp == 0) {
+            u32 ok = 1u;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(mb, tx);
+                ok = 0u;
+                for (u32 i = 0; i < LC_WAIT_TRIES && !ok; ++i) ok = mbar_try_wait(mb, (parity >> slot) & 1u);
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            __syncwarp();
+            if (lane == 0) {
+                const uint2 t = ctop[slot];  // stays zero in CTA 0
+                sC = t.x;
+                sY = t.y;
+            }
+            eC = eX = 0u;
+            for (u32 i = (u32)lane; i < ncta * (u32)nwarps; i += 32) {
+                const uint2 t = parts[slot][i];
+                eC ^= t.x;
+                eX ^= t.y;
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                eC ^= __shfl_xor_sync(0xffffffffu, eC, o);
+                eX ^= __shfl_xor_sync(0xffffffffu, eX, o);
+            }
+            const u32 EC = __brev(eC), EX = __brev(eX);
+            u32 A = 0x80000000u, B = 0u, A2 = 0u, B2 = 0x80000000u, dm = 0u, gm = 0u, over = 0u;
+            for (u32 u = 0; u < k; ++u) {
+                const u32 dmask = 0u - (u32)(__popc((A & EC) ^ (B & EX)) & 1);
+                const u32 gmask = dmask & (0u - (u32)(2 * L <= n + u));
+                const u32 Lg = n + u + 1 - L;
+                over |= gmask & (0u - (u32)(Lg >= W * 32));
+                const u32 nA = A ^ (A2 & dmask), nB = B ^ (B2 & dmask);
+                A2 = (A & gmask) | (A2 & ~gmask);
+                B2 = (B & gmask) | (B2 & ~gmask);
+                A = nA >> 1;
+                B = nB >> 1;
+                L = gmask ? Lg : L;
+                dm |= (dmask & 1u) << u;
+                gm |= (gmask & 1u) << u;
+            }
+            if (lane == 0) steps[slot] = make_uint4(dm, gm, L, ok ? (over ? 1u : 0u) : 2u);
+        }
+        parity ^= 1u << slot;
+        __syncthreads();
+        if (warp > 0 && lane == 0) {  // written by the previous warp's lane 31 before this barrier
+            const uint2 t = tops[slot][warp - 1];
+            sC = t.x;
+            sY = t.y;
+        }
+        const uint4 sd = steps[slot];
+        if (sd.w) {  // overflow: uniform across the cluster; timeout: this CTA gives up
+            if (g == 0 || sd.w == 2u) *job.out = sd.w == 2u ? ~1ull : ~0ull;
+            return;
+        }
+        L = sd.z;
+        if (w0 <= (D + 32) / 32) {
+            u32 ev = sd.x, tau = 0u;
+            while (ev) {
+                const u32 u = (u32)__ffs(ev) - 1u;
+                ev &= ev - 1u;
+                const u32 dl = u - tau;
+                const u32 sx = sY << dl;
+                if ((sd.y >> u) & 1u) {
+#pragma unroll
+                    for (int j = R - 1; j >= 0; --j) {
+                        const u32 xw = __funnelshift_l(j ? y[j - 1] : sY, y[j], dl);
+                        y[j] = c[j];
+                        c[j] ^= xw;
+                    }
+                    const u32 t = sC;
+                    sC ^= sx;
+                    sY = t;
+                    tau = u;
+                } else {
+#pragma unroll
+                    for (int j = R - 1; j >= 0; --j) c[j] ^= __funnelshift_l(j ? y[j - 1] : sY, y[j], dl);
+                    sC ^= sx;
+                }
+            }
+            const u32 sh = k - tau;
+#pragma unroll
+            for (int j = R - 1; j >= 0; --j) y[j] = __funnelshift_lc(j ? y[j - 1] : sY, y[j], sh);
+        }
+        n += k;
+        if (lane == 31) tops[slot ^ 1][warp] = make_uint2(c[R - 1], y[R - 1]);
+        slot ^= 1;
+    }
+    cluster_barrier();  // no CTA leaves while another may still store into it
+    if (g == 0) *job.out = (unsigned long long)L;
+}
+
+// Words per thread on a cluster: 2 up to 2048 words (about 131,000 bits), else
+// 4.  Measured on GB300 with clusters of 8: one 65,992-bit sequence 6.4, 5.8,
+// 6.9 ms at R = 1, 2, 4; one 699,464-bit sequence 102.7 and 92.8 ms at R = 2
+// and 4 (191.8 ms on one CTA).
+static int lc_r_cluster(u32 W) { return W <= 2048 ? 2 : 4; }
+
+template <int R>
+static cudaError_t launch_bm_cluster_r(const LcJob *d_jobs, unsigned count, u32 Wmax, cudaStream_t st)
+{
+    const unsigned per = (unsigned)(((Wmax + R * LC_CLUSTER - 1) / (R * LC_CLUSTER) + 31) / 32 * 32);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(count * LC_CLUSTER);
+    cfg.blockDim = dim3(per);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = LC_CLUSTER;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_berlekamp_massey_cluster<R>, d_jobs);
+    count_launch();
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Whether clusters of LC_CLUSTER CTAs of `threads` threads fit this device
+// (one resident at least).
+template <int R>
+static bool cluster_fits(unsigned threads)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(LC_CLUSTER);
+    cfg.blockDim = dim3(threads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = LC_CLUSTER;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k_berlekamp_massey_cluster<R>, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return nc >= 1;
+}
+
+static cudaError_t launch_bm_cluster(int R, const LcJob *d_jobs, unsigned count, u32 Wmax, cudaStream_t st)
+{
+    switch (R) {
+    case 1: return launch_bm_cluster_r<1>(d_jobs, count, Wmax, st);
+    case 2: return launch_bm_cluster_r<2>(d_jobs, count, Wmax, st);
+    case 4: return launch_bm_cluster_r<4>(d_jobs, count, Wmax, st);
+    default: return launch_bm_cluster_r<8>(d_jobs, count, Wmax, st);
+    }
+}
+
+static bool bm_cluster_fits(int R, u32 Wmax)
+{
+    const unsigned per = (unsigned)(((Wmax + R * LC_CLUSTER - 1) / (R * LC_CLUSTER) + 31) / 32 * 32);
+    switch (R) {
+    case 1: return cluster_fits<1>(per);
+    case 2: return cluster_fits<2>(per);
+    case 4: return cluster_fits<4>(per);
+    default: return cluster_fits<8>(per);
+    }
+}
+
 template <int V>
 static cudaError_t lc_bits_v(const u32 *tables, const LcJob *d_jobs, unsigned count, size_t max_threads,
                              cudaStream_t st)
@@ -426,10 +733,14 @@ static int lc_run(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, const void *
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) return XR_ECUDA;
     const bool many = njobs >= (size_t)sms;
+    // launch group of a job: words per thread, plus 100 for a cluster per
+    // sequence (few sequences, each longer than one warp's 256 words)
+    const bool clustered = njobs * LC_CLUSTER <= (size_t)sms;
+    auto group = [&](u32 W) { return clustered && W > 256 ? 100 + lc_r_cluster(W) : lc_r(W, many); };
     std::vector<size_t> order(njobs);
     for (size_t j = 0; j < njobs; ++j) order[j] = j;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
-        const int ra = lc_r(lc_words(jobs[a].N), many), rb = lc_r(lc_words(jobs[b].N), many);
+        const int ra = group(lc_words(jobs[a].N)), rb = group(lc_words(jobs[b].N));
         return ra != rb ? ra < rb : jobs[a].variant < jobs[b].variant;
     });
     char *base = (char *)d_scratch;
@@ -463,7 +774,7 @@ static int lc_run(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, const void *
     for (size_t i = 0; err == cudaSuccess && i < njobs;) {  // one launch per variant run
         size_t e = i, max_threads = 0;
         while (e < njobs && jobs[order[e]].variant == jobs[order[i]].variant &&
-               lc_r(h_jobs[e].W, many) == lc_r(h_jobs[i].W, many)) {
+               group(h_jobs[e].W) == group(h_jobs[i].W)) {
             max_threads = std::max(max_threads, ((size_t)h_jobs[e].N + h_jobs[e].chunk - 1) / h_jobs[e].chunk);
             ++e;
         }
@@ -472,20 +783,25 @@ static int lc_run(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, const void *
         i = e;
     }
     for (size_t i = 0; err == cudaSuccess && i < njobs;) {  // one launch per words-per-thread group
-        const int R = lc_r(h_jobs[i].W, many);
+        const int G = group(h_jobs[i].W);
         size_t e = i;
         u32 Wmax = 0;
-        while (e < njobs && lc_r(h_jobs[e].W, many) == R) {
+        while (e < njobs && group(h_jobs[e].W) == G) {
             Wmax = std::max(Wmax, h_jobs[e].W);
             ++e;
         }
-        err = launch_bm(R, d_jobs + i, (unsigned)(e - i), Wmax, st);
+        if (G >= 100 && bm_cluster_fits(G - 100, Wmax))
+            err = launch_bm_cluster(G - 100, d_jobs + i, (unsigned)(e - i), Wmax, st);
+        else
+            err = launch_bm(lc_r(Wmax, many), d_jobs + i, (unsigned)(e - i), Wmax, st);
         i = e;
     }
     std::vector<unsigned long long> res(njobs);
     if (err == cudaSuccess) err = cudaMemcpyAsync(res.data(), d_out, njobs * 8, cudaMemcpyDeviceToHost, st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) return XR_ECUDA;
+    for (size_t j = 0; j < njobs; ++j)
+        if (res[j] == ~1ull) return XR_ECUDA;  // a cluster's wait ran out
     for (size_t j = 0; j < njobs; ++j) h_lc[j] = res[j];
     return XR_OK;
 }
