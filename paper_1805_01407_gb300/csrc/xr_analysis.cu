@@ -134,6 +134,65 @@ __global__ void __launch_bounds__(128) k_lc_bits(const u32 *__restrict__ tables,
     }
 }
 
+// The same bits for runs of many sequences of one generator: lane l of a warp
+// is sequence 32 blockIdx.y + l of the run and the warp shares its chunk index
+// p, so every jump product is the same matrix for all lanes (broadcast column
+// loads, no divergence).  Chunks are 2^lg outputs; with the power sets of that
+// distance (P_l[j] = T^(2^lg j 512^l)) thread p starts at P_1[p >> 9] P_0[p & 511]
+// (p < 2048), else at the product of the tables T^(2^k) over the set bits of
+// p 2^lg.
+template <int V>
+__global__ void __launch_bounds__(128) k_lc_bits_many(const u32 *__restrict__ tables, const u32 *__restrict__ psets,
+                                                     const LcJob *__restrict__ jobs, unsigned count, u32 lg)
+{
+    typedef Gen<V> G;
+    typedef typename G::E E;
+    constexpr int n = E::NBITS, NW = n / 32;
+    const unsigned jx = blockIdx.y * 32 + (threadIdx.x & 31);
+    const size_t p = (size_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (jx >= count) return;
+    const LcJob job = jobs[jx];
+    const size_t N = job.N, t0 = p << lg;
+    if (t0 >= N) return;
+    E e;
+    load_state(e, job.state);
+    u32 v[NW], r[NW];
+    to_words(e, v);
+    if (psets) {
+        const u32 j0 = (u32)p & (PSET_SIZE - 1), j1 = (u32)(p >> PSET_BITS);
+        if (j0) {
+            f2_matvec<NW, false>(psets + (size_t)j0 * n * NW, v, r);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) v[w] = r[w];
+        }
+        if (j1) {
+            f2_matvec<NW, false>(psets + ((size_t)PSET_SIZE + j1) * n * NW, v, r);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) v[w] = r[w];
+        }
+    } else {
+        for (int k = 0; (t0 >> k) != 0; ++k) {
+            if (!((t0 >> k) & 1)) continue;
+            f2_matvec<NW, false>(tables + (size_t)k * n * NW, v, r);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) v[w] = r[w];
+        }
+    }
+    from_words(e, v);
+    const size_t t1 = t0 + ((size_t)1 << lg) < N ? t0 + ((size_t)1 << lg) : N;
+    const int bit = (int)job.bit;
+    u32 acc = 0u;
+    for (size_t t = t0; t < t1; ++t) {
+        const size_t pos = N - 1 - t;
+        acc |= (u32)((G::out(e) >> bit) & 1u) << (pos & 31);
+        e.step();
+        if ((pos & 31) == 0 || t + 1 == t1) {
+            atomicOr(job.rev + (pos >> 5), acc);
+            acc = 0u;
+        }
+    }
+}
+
 // One CTA per job, blocked Berlekamp-Massey: a barrier per block of (up to)
 // 32 sequence bits instead of one per bit.  Notation of the bit-serial
 // algorithm: C_n the connection polynomial, L_n its length, and
@@ -671,6 +730,30 @@ static cudaError_t lc_bits_v(const u32 *tables, const LcJob *d_jobs, unsigned co
     return cudaGetLastError();
 }
 
+template <int V>
+static cudaError_t lc_bits_many_v(const u32 *tables, const u32 *psets, const LcJob *d_jobs, unsigned count, u32 lg,
+                                  size_t nchunks, cudaStream_t st)
+{
+    const dim3 grid((unsigned)((nchunks + 3) / 4), (count + 31) / 32);
+    k_lc_bits_many<V><<<grid, 128, 0, st>>>(tables, psets, d_jobs, count, lg);
+    count_launch();
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_lc_bits_many(int variant, const u32 *tables, const u32 *psets, const LcJob *d_jobs,
+                                       unsigned count, u32 lg, size_t nchunks, cudaStream_t st)
+{
+    switch (variant) {
+#define XR_LC_CASE(V) \
+    case V: return lc_bits_many_v<V>(tables, psets, d_jobs, count, lg, nchunks, st);
+    XR_LC_CASE(0) XR_LC_CASE(1) XR_LC_CASE(2) XR_LC_CASE(3) XR_LC_CASE(4) XR_LC_CASE(5)
+    XR_LC_CASE(6) XR_LC_CASE(7) XR_LC_CASE(8) XR_LC_CASE(9) XR_LC_CASE(10) XR_LC_CASE(11)
+    XR_LC_CASE(12) XR_LC_CASE(13) XR_LC_CASE(14) XR_LC_CASE(15) XR_LC_CASE(16) XR_LC_CASE(17)
+#undef XR_LC_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 static cudaError_t launch_lc_bits(int variant, const u32 *tables, const LcJob *d_jobs, unsigned count,
                                   size_t max_threads, cudaStream_t st)
 {
@@ -779,7 +862,18 @@ static int lc_run(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, const void *
             ++e;
         }
         const int v = jobs[order[i]].variant;
-        err = launch_lc_bits(v, ctx->tables[lc_engine_of(v)], d_jobs + i, (unsigned)(e - i), max_threads, st);
+        const int eng = lc_engine_of(v);
+        if (e - i >= 32) {  // a run of many sequences: one sequence per lane
+            size_t Nmax = 0;
+            for (size_t k = i; k < e; ++k) Nmax = std::max(Nmax, (size_t)h_jobs[k].N);
+            u32 lg = 8;  // chunks of 2^lg >= 256 outputs, at most 2048 per sequence
+            while ((Nmax + ((size_t)1 << lg) - 1) >> lg > 2048) ++lg;
+            const u32 *ps = eng < NUM_PSET_ENGINES ? dist_sets(ctx, eng, (int)lg) : nullptr;
+            err = launch_lc_bits_many(v, ctx->tables[eng], ps, d_jobs + i, (unsigned)(e - i), lg,
+                                      (Nmax + ((size_t)1 << lg) - 1) >> lg, st);
+        } else {
+            err = launch_lc_bits(v, ctx->tables[eng], d_jobs + i, (unsigned)(e - i), max_threads, st);
+        }
         i = e;
     }
     for (size_t i = 0; err == cudaSuccess && i < njobs;) {  // one launch per words-per-thread group
