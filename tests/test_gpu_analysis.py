@@ -187,3 +187,51 @@ def test_linear_complexity_bulk_configuration_full(ctx, xr):
         if b == 0 and v.endswith("+") and not v.endswith("++"):
             assert got[k] == O.state_bits(v), v
         assert got[k] is not None and 0 < got[k] <= N // 2 + 64
+
+
+def _oracle_all(jobs, seeds):
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with ThreadPoolExecutor(cores) as ex:
+        return list(ex.map(lambda a: O.linear_complexity(a[0][0], a[0][1], a[0][2], a[1]), zip(jobs, seeds)))
+
+
+def test_linear_complexity_cluster_threshold(ctx, xr):
+    """Calls of up to SMs / 8 sequences run each sequence on a cluster of 8
+    CTAs, larger calls one CTA per sequence: the same mixed jobs (lengths from
+    300 to 60000 bits, low and high bits, every engine size) at the threshold
+    and one above it, against the oracle, and the first jobs against the
+    single call (which also takes the cluster path)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    k = sms // 8
+    rng = np.random.default_rng(23)
+    jobs, seeds = [], []
+    for j in range(k + 1):
+        v = W.ALL_VARIANTS[(3 * j) % len(W.ALL_VARIANTS)]
+        jobs.append((v, int(rng.integers(0, O.word_bits(v))), int(np.exp(rng.uniform(np.log(300), np.log(60000))))))
+        seeds.append(int(rng.integers(1, 1 << 40)))
+    want = _oracle_all(jobs, seeds)
+    for m in (k, k + 1):
+        got = ctx.linear_complexity_many(jobs[:m], states_for(ctx, xr, jobs[:m], seeds[:m]))
+        assert got == want[:m], m
+    for j in range(3):
+        v, bit, N = jobs[j]
+        assert ctx.linear_complexity(v, bit, N, seeded(ctx, v, seeds[j])) == want[j]
+
+
+@pytest.mark.parametrize("name,count,Nmax", [("xoshiro256**", 40, 70000), ("xoroshiro1024++", 33, 20000)])
+def test_linear_complexity_many_long_run_of_one_generator(ctx, xr, name, count, Nmax):
+    """A run of at least 32 sequences of one generator takes the bit kernel
+    with one sequence per lane: lengths from 2 to Nmax in one run (sequences
+    that end in different chunks, and in the first), with and without the
+    engine's power sets (xoroshiro1024 jumps with its T^(2^k) tables)."""
+    rng = np.random.default_rng(count)
+    jobs, seeds = [], []
+    for j in range(count):
+        N = 2 if j == 0 else (Nmax if j == 1 else int(np.exp(rng.uniform(np.log(2), np.log(Nmax)))))
+        jobs.append((name, int(rng.integers(0, O.word_bits(name))), N))
+        seeds.append(int(rng.integers(1, 1 << 40)))
+    got = ctx.linear_complexity_many(jobs, states_for(ctx, xr, jobs, seeds))
+    assert got == _oracle_all(jobs, seeds)
