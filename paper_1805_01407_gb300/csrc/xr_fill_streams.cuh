@@ -17,20 +17,24 @@ namespace xr {
 // P_0[j] once, and the lanes of each warp are 32 consecutive parents, hence
 // 32 consecutive streams (rows p0 + P j ..), written by 2D tile stores like
 // k_fill_tma.  The start states never reach global memory.  A warp takes
-// FS_GROUPS groups of 32 parents in turn, so the tile stores of one group
+// `groups` groups of 32 parents in turn, so the tile stores of one group
 // drain while the next group's products run; for doubles of 64-bit words a
 // lane also keeps its start state in a shared-memory slot, for the rare exact
-// redo of a row.  One tile
-// per warp and 16 warps per CTA measured best (2^24 x 64: u64 1.63 ms, f64
-// 1.81 ms; 8 warps x 1 tile 1.64 / 1.88 ms; 8 warps x 2 tiles, u64 1.73 ms):
-// shared memory, not the store queue, limits the warps per SM.  Only rows
+// redo of a row.  One tile per warp and 16 warps per CTA measured best (2^24
+// x 64, 4 groups: u64 1.63 ms, f64 1.81 ms; 8 warps x 1 tile 1.64 / 1.88 ms;
+// 8 warps x 2 tiles, u64 1.73 ms): shared memory, not the store queue, limits
+// the warps per SM.  More groups per CTA spread each table build over more
+// streams but leave fewer CTAs for the tail, so the count is a template
+// argument: 8 from 2^15 parents (2^24 streams) on, else 4 (2^24 x 64 u64 with
+// 2, 3, 4, 6, 8, 10, 12, 16 groups: 1.635, 1.617, 1.612, 1.577, 1.547, 1.561,
+// 1.554, 1.588 ms; 2^21 x 64 u64 with 4 and 8 groups: 0.249 and 0.267 ms; a
+// count passed at run time cost 2 % on the doubles).  Only rows
 // of at most FILL_SHORT_TILES tiles come here: for longer rows the start
 // states are a small part of the work, and a state table followed by the
 // fill's own configuration (many small CTAs for the exact doubles, which a
 // resident 32 KB table rules out) measured faster.
 constexpr int FS_WARPS = 16;
 constexpr int FS_NBUF = 1;
-constexpr int FS_GROUPS = 4;  // groups of 32 parents per warp, one after another
 constexpr int FS_CHILDREN = PSET_SIZE;  // streams per parent (j < 512)
 
 template <int V>
@@ -41,7 +45,7 @@ struct FuseCfg {
     static constexpr int SMEM = FS_WARPS * FS_NBUF * TILE_BYTES + TABLE_BYTES + FS_WARPS * 32 * 32 + 1024;
 };
 
-template <int V, int DT>
+template <int V, int DT, int GROUPS>
 __global__ void __launch_bounds__(FS_WARPS * 32)
     k_fill_streams(const __grid_constant__ CUtensorMap map, const u32 *__restrict__ P0, const u32 *parents,
                    size_t npar, size_t m, int *status)  // npar = P
@@ -63,8 +67,8 @@ __global__ void __launch_bounds__(FS_WARPS * 32)
     const u32 tiles = base + (u32)(warp * FS_NBUF * TILE_BYTES);
     unsigned char *slot = slots + (warp * 32 + lane) * 32;
     int it = 0;
-    for (int g = 0; g < FS_GROUPS; ++g) {
-        const size_t p0 = (((size_t)blockIdx.y * FS_GROUPS + g) * FS_WARPS + warp) * 32;
+    for (int g = 0; g < GROUPS; ++g) {
+        const size_t p0 = (((size_t)blockIdx.y * GROUPS + g) * FS_WARPS + warp) * 32;
         if (p0 >= npar) break;
         const bool live = p0 + lane < npar;
         u32 v[NW], r[NW];
@@ -132,7 +136,9 @@ cudaError_t launch_fill_streams_vd(const u32 *P0, const void *parents, size_t np
     const bool rows_ok = m > 0 && (m * ES) % 16 == 0 && (m + COLS - 1) / COLS <= (size_t)FILL_SHORT_TILES;
     const bool parents_ok = npar >= 32 && (npar & (npar - 1)) == 0 && (size_t)FS_CHILDREN * npar < (1ull << 31);
     if (!encode || ((uintptr_t)out % 16) || !rows_ok || !parents_ok) return cudaErrorNotSupported;
-    const size_t gy = (npar + FS_GROUPS * FS_WARPS * 32 - 1) / (FS_GROUPS * FS_WARPS * 32);
+    // groups per CTA: 4, or 8 from 2^15 parents (2^24 streams) on
+    const int groups = npar >= 32768 ? 8 : 4;
+    const size_t gy = (npar + (size_t)groups * FS_WARPS * 32 - 1) / ((size_t)groups * FS_WARPS * 32);
     if (gy > 65535) return cudaErrorNotSupported;
     CUtensorMap map;
     const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)(FS_CHILDREN * npar)};
@@ -143,11 +149,15 @@ cudaError_t launch_fill_streams_vd(const u32 *P0, const void *parents, size_t np
                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorNotSupported;
-    static std::atomic<uint64_t> attr{0};
-    const cudaError_t ea = set_smem_once(attr, k_fill_streams<V, DT>, FC::SMEM);
+    static std::atomic<uint64_t> attr4{0}, attr8{0};
+    cudaError_t ea = set_smem_once(attr4, k_fill_streams<V, DT, 4>, FC::SMEM);
+    if (ea == cudaSuccess) ea = set_smem_once(attr8, k_fill_streams<V, DT, 8>, FC::SMEM);
     if (ea != cudaSuccess) return ea;
-    k_fill_streams<V, DT><<<dim3(FS_CHILDREN, (unsigned)gy), FS_WARPS * 32, FC::SMEM, stream>>>(
-        map, P0, (const u32 *)parents, npar, m, status);
+    const dim3 grid(FS_CHILDREN, (unsigned)gy);
+    if (groups == 8)
+        k_fill_streams<V, DT, 8><<<grid, FS_WARPS * 32, FC::SMEM, stream>>>(map, P0, (const u32 *)parents, npar, m, status);
+    else
+        k_fill_streams<V, DT, 4><<<grid, FS_WARPS * 32, FC::SMEM, stream>>>(map, P0, (const u32 *)parents, npar, m, status);
     count_launch();
     return cudaGetLastError();
 }
