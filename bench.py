@@ -1140,9 +1140,9 @@ def run_profile_fill_jobs(args):
 
 
 def run_profile_lc(args):
-    """Linear complexity for ncu: lc = the largest Table 13 row (one CTA),
-    lc-bulk = the bulk configuration (448 CTAs); one warm-up call, then
-    --profile-launches calls."""
+    """Linear complexity for ncu: lc = the largest Table 13 row (one cluster
+    of 8 CTAs), lc-bulk = the bulk configuration (448 CTAs); one warm-up
+    call, then --profile-launches calls."""
     import torch
     import paper_1805_01407_gb300 as xr
     with xr.Context(0) as ctx:
