@@ -235,3 +235,31 @@ def test_linear_complexity_many_long_run_of_one_generator(ctx, xr, name, count, 
         seeds.append(int(rng.integers(1, 1 << 40)))
     got = ctx.linear_complexity_many(jobs, states_for(ctx, xr, jobs, seeds))
     assert got == _oracle_all(jobs, seeds)
+
+
+def test_linear_complexity_one_cta_long_sequences(ctx, xr):
+    """Calls of more than SMs / 8 sequences run one CTA per sequence; long
+    ones there take 8 words per thread (up to 8192 words) or 12 (beyond):
+    three sequences of 600,000 to 786,000 bits and two of 300,000 and
+    400,000 among short ones, against the oracle."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    count = sms // 8 + 1
+    long_ = [("xoroshiro128+", 1, 600001), ("xoshiro256+", 1, 700000), ("xoroshiro128+", 2, 786000),
+             ("xoshiro256**", 30, 300000), ("xoroshiro128++", 5, 400000)]
+    rng = np.random.default_rng(31)
+    jobs = list(long_)
+    while len(jobs) < count:
+        v = W.ALL_VARIANTS[len(jobs) % len(W.ALL_VARIANTS)]
+        jobs.append((v, int(rng.integers(0, O.word_bits(v))), int(rng.integers(2, 5000))))
+    seeds = [int(rng.integers(1, 1 << 40)) for _ in jobs]
+    got = ctx.linear_complexity_many(jobs, states_for(ctx, xr, jobs, seeds))
+    assert got == _oracle_all(jobs, seeds)
+
+
+@pytest.mark.parametrize("N", [64 * (2048 - 5), 64 * (2049 - 5)])
+def test_linear_complexity_cluster_words_per_thread_boundary(ctx, N):
+    """Single calls (cluster kernel) on both sides of its change from 2 to 4
+    words per thread (2048 polynomial words)."""
+    for name, bit in (("xoshiro256**", 11), ("xoroshiro128+", 0)):
+        assert ctx.linear_complexity(name, bit, N, seeded(ctx, name, 4)) == O.linear_complexity(name, bit, N, 4)
