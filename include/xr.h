@@ -458,8 +458,11 @@ int xr_zeroland(xr_ctx *ctx, int variant, size_t nout, size_t window, uint64_t *
  * complexity when N >= 2 L.  XR_EINVAL for bad arguments or N outside
  * 2 .. XR_LC_MAX_BITS.  A prefix complexity of 32 (floor(N / 64) + 5) or more
  * (above N / 2 + 127, so not decided by an N-bit prefix) returns
- * XR_EUNSUPPORTED.  One CTA with every polynomial and the sequence window in
- * registers; calls on different streams run concurrently. */
+ * XR_EUNSUPPORTED.  The polynomials stay in registers; the algorithm takes
+ * blocks of 32 sequence bits per synchronisation.  A sequence of 16,128 bits
+ * or more runs on a thread-block cluster of 8 CTAs (8 SMs), a shorter one on
+ * one CTA; XR_ECUDA also covers a cluster whose internal exchange did not
+ * complete (not expected).  Calls on different streams run concurrently. */
 #define XR_LC_MAX_BITS ((size_t)786000)
 #define XR_LC_SCRATCH_BYTES(N) (64 + ((((N) + 31) / 32 + 22) * 4 + 15) / 16 * 16)
 int xr_linear_complexity(xr_ctx *ctx, int variant, int bit, size_t N, const void *d_state, void *d_scratch,
@@ -468,8 +471,10 @@ int xr_linear_complexity(xr_ctx *ctx, int variant, int bit, size_t N, const void
 /* Many linear complexities in one call: job j takes the state at d_states +
  * j * state_stride (device, 16-byte aligned; the stride a multiple of 16 and
  * at least the largest state) and gives h_lc[j] (host): the complexity, or
- * UINT64_MAX where xr_linear_complexity would return XR_EUNSUPPORTED.  One CTA
- * per job, so up to a few hundred jobs run at once.  d_scratch (device,
+ * UINT64_MAX where xr_linear_complexity would return XR_EUNSUPPORTED.  With
+ * at most (SMs / 8) jobs each sequence of 16,128 bits or more runs on a
+ * cluster of 8 CTAs; otherwise one CTA per job, so up to a few hundred jobs
+ * run at once.  d_scratch (device,
  * 16-byte aligned) must hold xr_lc_scratch_bytes(jobs, njobs) bytes.  Any bad
  * job makes the call return XR_EINVAL before work is enqueued.  Waits for the
  * device. */
