@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import struct
 
 __all__ = ["Context", "XRError", "VARIANTS", "DTYPES", "state_words", "word_bits", "state_bytes",
            "state_bits", "jump_log2", "lib", "library_path"]
@@ -62,6 +63,10 @@ class Request(ctypes.Structure):
 class LcJob(ctypes.Structure):
     """xr_lc_job of include/xr.h."""
     _fields_ = [("variant", ctypes.c_int32), ("bit", ctypes.c_int32), ("N", ctypes.c_uint64)]
+
+
+_LC_RECORD = struct.Struct("<iiQ")  # one LcJob
+assert _LC_RECORD.size == ctypes.sizeof(LcJob)
 
 
 class XRError(RuntimeError):
@@ -172,20 +177,34 @@ def _v(variant):
     return int(variant)
 
 
+_PROPERTIES = {}
+
+
+def _property(name, variant):
+    """A pure property of a generator from libxr, asked once per (property,
+    variant): the per-job checks of a call with hundreds of jobs would
+    otherwise cost a foreign call each."""
+    key = (name, _v(variant))
+    value = _PROPERTIES.get(key)
+    if value is None:
+        value = _PROPERTIES[key] = getattr(lib(), name)(key[1])
+    return value
+
+
 def state_words(variant):
-    return lib().xr_state_words(_v(variant))
+    return _property("xr_state_words", variant)
 
 
 def word_bits(variant):
-    return lib().xr_word_bits(_v(variant))
+    return _property("xr_word_bits", variant)
 
 
 def state_bytes(variant):
-    return lib().xr_state_bytes(_v(variant))
+    return _property("xr_state_bytes", variant)
 
 
 def state_bits(variant):
-    return lib().xr_state_bits(_v(variant))
+    return _property("xr_state_bits", variant)
 
 
 def jump_log2(variant, kind="jump"):
@@ -418,11 +437,14 @@ class Context:
         j reads its state at byte j * state_stride of d_states.  Returns a list
         of ints, None where N bits cannot decide the complexity."""
         import torch
-        arr = (LcJob * max(len(jobs), 1))(*[LcJob(_v(v), b, n) for (v, b, n) in jobs])
-        if state_stride % 16 or any(state_stride < state_bytes(v) for (v, _, _) in jobs[:-1]):
+        # the records packed in one pass (xr_lc_job: int32 variant, int32 bit, uint64 N)
+        arr = (LcJob * max(len(jobs), 1)).from_buffer_copy(
+            b"".join([_LC_RECORD.pack(_v(v), b, n) for (v, b, n) in jobs]) or bytes(ctypes.sizeof(LcJob)))
+        sb = {v: state_bytes(v) for v in {v for (v, _, _) in jobs}}
+        if state_stride % 16 or any(state_stride < sb[v] for v in {v for (v, _, _) in jobs[:-1]}):
             raise ValueError("state_stride must be a multiple of 16 and hold every state")
-        _need(d_states, max((j * state_stride + state_bytes(v) for j, (v, _, _) in enumerate(jobs)), default=0),
-              "d_states")
+        # every state but the last fits its stride, so the last one ends furthest
+        _need(d_states, (len(jobs) - 1) * state_stride + sb[jobs[-1][0]] if jobs else 0, "d_states")
         nbytes = lib().xr_lc_scratch_bytes(arr, len(jobs))
         scratch = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=self.device)
         out = (ctypes.c_uint64 * max(len(jobs), 1))()
