@@ -460,9 +460,10 @@ int xr_zeroland(xr_ctx *ctx, int variant, size_t nout, size_t window, uint64_t *
  * (above N / 2 + 127, so not decided by an N-bit prefix) returns
  * XR_EUNSUPPORTED.  The polynomials stay in registers; the algorithm takes
  * blocks of 32 sequence bits per synchronisation.  A sequence of 16,128 bits
- * or more runs on a thread-block cluster of 8 CTAs (8 SMs), a shorter one on
- * one CTA; XR_ECUDA also covers a cluster whose internal exchange did not
- * complete (not expected).  Calls on different streams run concurrently. */
+ * or more runs on a thread-block cluster of 16 CTAs (16 SMs; 8 where the
+ * device does not take 16), a shorter one on one CTA; XR_ECUDA also covers a
+ * cluster whose internal exchange did not complete (not expected).  Calls on
+ * different streams run concurrently. */
 #define XR_LC_MAX_BITS ((size_t)786000)
 #define XR_LC_SCRATCH_BYTES(N) (64 + ((((N) + 31) / 32 + 22) * 4 + 15) / 16 * 16)
 int xr_linear_complexity(xr_ctx *ctx, int variant, int bit, size_t N, const void *d_state, void *d_scratch,
@@ -473,10 +474,10 @@ int xr_linear_complexity(xr_ctx *ctx, int variant, int bit, size_t N, const void
  * at least the largest state) and gives h_lc[j] (host): the complexity, or
  * UINT64_MAX where xr_linear_complexity would return XR_EUNSUPPORTED.  With
  * at most (SMs / 8) jobs each sequence of 16,128 bits or more runs on a
- * cluster of 8 CTAs; otherwise one CTA per job, so up to a few hundred jobs
- * run at once.  d_scratch (device,
- * 16-byte aligned) must hold xr_lc_scratch_bytes(jobs, njobs) bytes.  Any bad
- * job makes the call return XR_EINVAL before work is enqueued.  Waits for the
+ * cluster of 8 CTAs (16 with at most SMs / 16 jobs); otherwise one CTA per
+ * job, so up to a few hundred jobs run at once.  d_scratch (device, 16-byte
+ * aligned) must hold xr_lc_scratch_bytes(jobs, njobs) bytes.  Any bad job
+ * makes the call return XR_EINVAL before work is enqueued.  Waits for the
  * device. */
 typedef struct xr_lc_job {
     int32_t variant;

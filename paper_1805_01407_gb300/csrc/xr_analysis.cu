@@ -416,7 +416,7 @@ static cudaError_t launch_bm(int R, const LcJob *d_jobs, unsigned count, u32 Wma
 // ---------------------------------------------------------------- one sequence on a cluster of CTAs
 //
 // The same blocked algorithm for calls with few sequences, which would leave
-// most SMs idle with one CTA each: a cluster of LC_CLUSTER CTAs (one per SM)
+// most SMs idle with one CTA each: a cluster of 16 or 8 CTAs (one per SM)
 // shares a sequence, global thread g = rank * blockDim + tid holding words
 // gR .. gR+R-1.  Per block, every warp sends its lookahead masks to every
 // CTA of the cluster with st.async, which lands them in that CTA's shared
@@ -432,7 +432,7 @@ static cudaError_t launch_bm(int R, const LcJob *d_jobs, unsigned count, u32 Wma
 // (no CTA leaves while another may still store into it).  A wait that runs out
 // (LC_WAIT_TRIES polls) makes its CTA report ~1, which the call turns into an
 // error, and return.
-constexpr unsigned LC_CLUSTER = 8;
+constexpr unsigned LC_CLUSTER = 8, LC_CLUSTER_MAX = 16;
 
 __device__ __forceinline__ u32 cluster_ctarank()
 {
@@ -507,7 +507,7 @@ constexpr u32 LC_WAIT_TRIES = 1u << 24;
 template <int R>
 __global__ void __launch_bounds__(1024) k_berlekamp_massey_cluster(const LcJob *__restrict__ jobs)
 {
-    __shared__ uint2 parts[2][LC_CLUSTER * 32];  // [slot][rank * nwarps + warp]: every warp's e_C, e_X
+    __shared__ uint2 parts[2][LC_CLUSTER_MAX * 32];  // [slot][rank * nwarps + warp]: every warp's e_C, e_X
     __shared__ uint2 tops[2][32];                // [slot][warp]: top words of C, Y of the warp's lane 31
     __shared__ uint2 ctop[2];                    // [slot]: top words of the previous CTA's last thread
     __shared__ uint4 steps[2];                   // [slot]: d mask, length-change mask, L, overflow / timeout
@@ -649,48 +649,51 @@ __global__ void __launch_bounds__(1024) k_berlekamp_massey_cluster(const LcJob *
     if (g == 0) *job.out = (unsigned long long)L;
 }
 
-// Words per thread on a cluster: 2 up to 2048 words (about 131,000 bits), else
-// 4.  Measured on GB300 with clusters of 8: one 65,992-bit sequence 6.4, 5.8,
-// 6.9 ms at R = 1, 2, 4; one 699,464-bit sequence 102.7 and 92.8 ms at R = 2
-// and 4 (191.8 ms on one CTA).
-static int lc_r_cluster(u32 W) { return W <= 2048 ? 2 : 4; }
+// Clusters of LC_CLUSTER_MAX CTAs (a non-portable size, allowed per kernel)
+// where the device takes them and the call has few enough sequences, else
+// LC_CLUSTER.  Words
+// per thread: 2 on 16 CTAs; on 8, 2 up to 2048 words (about 131,000 bits),
+// else 4.  Measured on GB300: one 699,464-bit sequence 92.8 ms on 8 CTAs (R = 4;
+// 102.7 at R = 2), 77.7 ms on 16 (R = 2; 80.2 at R = 4, 98.0 at R = 1), 191.8 ms
+// on one CTA; one 65,992-bit sequence 5.8 ms on 8 or 16 CTAs (R = 2; 6.4 and
+// 6.9 ms at R = 1 and 4 on 8).
+static int lc_r_cluster(u32 W, unsigned ncta) { return ncta >= 16 || W <= 2048 ? 2 : 4; }
 
-template <int R>
-static cudaError_t launch_bm_cluster_r(const LcJob *d_jobs, unsigned count, u32 Wmax, cudaStream_t st)
+static unsigned lc_cluster_threads(u32 Wmax, int R, unsigned ncta)
 {
-    const unsigned per = (unsigned)(((Wmax + R * LC_CLUSTER - 1) / (R * LC_CLUSTER) + 31) / 32 * 32);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(count * LC_CLUSTER);
-    cfg.blockDim = dim3(per);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = LC_CLUSTER;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_berlekamp_massey_cluster<R>, d_jobs);
-    count_launch();
-    return e != cudaSuccess ? e : cudaGetLastError();
+    return (unsigned)(((Wmax + R * ncta - 1) / (R * ncta) + 31) / 32 * 32);
 }
 
-// Whether clusters of LC_CLUSTER CTAs of `threads` threads fit this device
-// (one resident at least).
-template <int R>
-static bool cluster_fits(unsigned threads)
+static cudaLaunchConfig_t lc_cluster_config(unsigned count, unsigned threads, unsigned ncta, cudaStream_t st,
+                                            cudaLaunchAttribute *attr)
 {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(LC_CLUSTER);
+    cfg.gridDim = dim3(count * ncta);
     cfg.blockDim = dim3(threads);
-    cudaLaunchAttribute attr[1];
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = LC_CLUSTER;
+    attr[0].val.clusterDim.x = ncta;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    return cfg;
+}
+
+// Whether clusters of ncta CTAs of `threads` threads fit this device (one
+// resident at least); sizes above 8 are first allowed for the kernel.
+template <int R>
+static bool cluster_fits(unsigned threads, unsigned ncta)
+{
+    if (ncta > 8 &&
+        cudaFuncSetAttribute(k_berlekamp_massey_cluster<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = lc_cluster_config(1, threads, ncta, nullptr, attr);
     int nc = 0;
     if (cudaOccupancyMaxActiveClusters(&nc, k_berlekamp_massey_cluster<R>, &cfg) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -699,25 +702,34 @@ static bool cluster_fits(unsigned threads)
     return nc >= 1;
 }
 
-static cudaError_t launch_bm_cluster(int R, const LcJob *d_jobs, unsigned count, u32 Wmax, cudaStream_t st)
+template <int R>
+static cudaError_t launch_bm_cluster_r(const LcJob *d_jobs, unsigned count, u32 Wmax, unsigned ncta,
+                                       cudaStream_t st)
 {
-    switch (R) {
-    case 1: return launch_bm_cluster_r<1>(d_jobs, count, Wmax, st);
-    case 2: return launch_bm_cluster_r<2>(d_jobs, count, Wmax, st);
-    case 4: return launch_bm_cluster_r<4>(d_jobs, count, Wmax, st);
-    default: return launch_bm_cluster_r<8>(d_jobs, count, Wmax, st);
-    }
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = lc_cluster_config(count, lc_cluster_threads(Wmax, R, ncta), ncta, st, attr);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_berlekamp_massey_cluster<R>, d_jobs);
+    count_launch();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-static bool bm_cluster_fits(int R, u32 Wmax)
+// Launches the jobs on clusters when some size fits (first LC_CLUSTER_MAX if
+// count allows, then LC_CLUSTER); *launched = false when none does.
+static cudaError_t launch_bm_cluster(const LcJob *d_jobs, unsigned count, u32 Wmax, int sms, cudaStream_t st,
+                                     bool *launched)
 {
-    const unsigned per = (unsigned)(((Wmax + R * LC_CLUSTER - 1) / (R * LC_CLUSTER) + 31) / 32 * 32);
-    switch (R) {
-    case 1: return cluster_fits<1>(per);
-    case 2: return cluster_fits<2>(per);
-    case 4: return cluster_fits<4>(per);
-    default: return cluster_fits<8>(per);
+    *launched = false;
+    for (unsigned ncta : {LC_CLUSTER_MAX, LC_CLUSTER}) {
+        if ((size_t)count * ncta > (size_t)sms) continue;
+        const int R = lc_r_cluster(Wmax, ncta);
+        const unsigned threads = lc_cluster_threads(Wmax, R, ncta);
+        const bool fits = R == 2 ? cluster_fits<2>(threads, ncta) : cluster_fits<4>(threads, ncta);
+        if (!fits) continue;
+        *launched = true;
+        return R == 2 ? launch_bm_cluster_r<2>(d_jobs, count, Wmax, ncta, st)
+                      : launch_bm_cluster_r<4>(d_jobs, count, Wmax, ncta, st);
     }
+    return cudaSuccess;
 }
 
 template <int V>
@@ -819,7 +831,7 @@ static int lc_run(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, const void *
     // launch group of a job: words per thread, plus 100 for a cluster per
     // sequence (few sequences, each longer than one warp's 256 words)
     const bool clustered = njobs * LC_CLUSTER <= (size_t)sms;
-    auto group = [&](u32 W) { return clustered && W > 256 ? 100 + lc_r_cluster(W) : lc_r(W, many); };
+    auto group = [&](u32 W) { return clustered && W > 256 ? 100 : lc_r(W, many); };
     std::vector<size_t> order(njobs);
     for (size_t j = 0; j < njobs; ++j) order[j] = j;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
@@ -884,9 +896,9 @@ static int lc_run(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, const void *
             Wmax = std::max(Wmax, h_jobs[e].W);
             ++e;
         }
-        if (G >= 100 && bm_cluster_fits(G - 100, Wmax))
-            err = launch_bm_cluster(G - 100, d_jobs + i, (unsigned)(e - i), Wmax, st);
-        else
+        bool on_clusters = false;
+        if (G >= 100) err = launch_bm_cluster(d_jobs + i, (unsigned)(e - i), Wmax, sms, st, &on_clusters);
+        if (err == cudaSuccess && !on_clusters)
             err = launch_bm(lc_r(Wmax, many), d_jobs + i, (unsigned)(e - i), Wmax, st);
         i = e;
     }
