@@ -823,13 +823,14 @@ static int lc_run(xr_ctx *ctx, const xr_lc_job *jobs, size_t njobs, const void *
         const int rc = ensure_engine(ctx, eng);
         if (rc != XR_OK) return rc;
     }
-    // jobs ordered by (words per thread, variant): one Berlekamp-Massey launch
-    // per words-per-thread group, one bit-generation launch per variant run
+    // jobs ordered by (launch group, variant): one Berlekamp-Massey launch per
+    // group, one bit-generation launch per variant run
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) return XR_ECUDA;
     const bool many = njobs >= (size_t)sms;
-    // launch group of a job: words per thread, plus 100 for a cluster per
-    // sequence (few sequences, each longer than one warp's 256 words)
+    // launch group of a job: its words per thread on one CTA, or 100 for a
+    // cluster per sequence (few sequences, each longer than one warp's 256
+    // words; the cluster size and words per thread are chosen at launch)
     const bool clustered = njobs * LC_CLUSTER <= (size_t)sms;
     auto group = [&](u32 W) { return clustered && W > 256 ? 100 : lc_r(W, many); };
     std::vector<size_t> order(njobs);
