@@ -1,4 +1,5 @@
-// xr_analysis.cu -- the paper's analysis workloads on the device.
+// xr_analysis.cu -- the paper's analysis workloads on the device: escaping
+// zeroland and linear complexity.
 //
 // Escaping zeroland (Sec. 8): starting from each of the n states with
 // exactly one bit set, how fast do the outputs reach half ones?  One thread
@@ -76,10 +77,10 @@ cudaError_t launch_zeroland(int variant, size_t nout, int window, unsigned long 
 //
 // Berlekamp-Massey over F2 (Sec. 9.3; the paper computes Table 13's lowest
 // values this way) on bit `bit` of the first N outputs of a sequence, for many
-// sequences at once: one CTA per sequence.  The bits are stored reversed and
-// packed (bit j of rev = s_{N-1-j}), so the window s_n, s_{n-1}, ..., s_{n-L}
-// lines up with the connection polynomial's coefficients c_0 .. c_L starting
-// at bit N-1-n.
+// sequences at once: one CTA per sequence, or a cluster of CTAs per sequence
+// when a call has few.  The bits are stored reversed and packed (bit j of
+// rev = s_{N-1-j}), so the window s_n, s_{n-1}, ..., s_{n-L} lines up with the
+// connection polynomial's coefficients c_0 .. c_L starting at bit N-1-n.
 
 static constexpr u32 LC_REV_PAD = 20;  // zero words after a sequence
 
