@@ -36,6 +36,7 @@ METRIC = "generated GB/s & % of HBM roofline (batched vs plain, 1 GB300); p50/p9
 UNIT = "GB/s"
 FILL_SOURCES = ("paper_1805_01407_gb300/csrc/xr_fill_impl.cuh", "paper_1805_01407_gb300/csrc/xr_device.cuh")
 FUSED_SOURCES = FILL_SOURCES + ("paper_1805_01407_gb300/csrc/xr_fill_streams.cuh", "paper_1805_01407_gb300/csrc/xr_f2.cuh")
+LC_SOURCES = ("paper_1805_01407_gb300/csrc/xr_analysis.cu",)
 
 
 def parse_args():
@@ -230,6 +231,25 @@ def recorded_fused_counts():
             return None
         return {"alu_lane_ops_per_stream": float(kv["alu_lane_ops_per_stream"]),
                 "shared_wavefronts_per_stream": float(kv["shared_wavefronts_per_stream"])}
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def recorded_lc_alu_ops():
+    """ALU-pipe lane operations of one Berlekamp-Massey launch of the bulk
+    linear-complexity configuration (448 sequences x 2^16 bits), from the
+    committed ncu summary, if taken on the current source; else None."""
+    path = os.path.join(ROOT, "profiles", "berlekamp_massey__bulk_448x65536.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#") and not line.startswith(" "):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha") != fill_source_hash(LC_SOURCES):
+            return None
+        return float(kv["alu_lane_ops_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -598,7 +618,7 @@ def run_xr(args):
     if not args.no_extra:
         line["layouts_and_types"] = run_layouts(xr, ctx, wc)
     if not args.no_analysis:
-        line["analysis"] = run_analysis(xr, ctx, args)
+        line["analysis"] = run_analysis(xr, ctx, args, ac)
     if not args.no_e2e:
         line["e2e"] = run_e2e(ctx, args, first, bytes_per_step, world, dist)
     if dist:
@@ -761,7 +781,7 @@ ANALYSIS_LC_SMALL = ("xoshiro256+", 1, 2 * 32896 + 200)
 ANALYSIS_LC_LARGE = ("xoroshiro128+", 2, 2 * 349632 + 200)
 
 
-def run_analysis(xr, ctx, args):
+def run_analysis(xr, ctx, args, ac=None):
     """The paper's analysis workloads: escaping zeroland (Sec. 8; all one-bit
     states of xoshiro256**, 1000 outputs, windows of 4) timed with events, and
     Berlekamp-Massey linear complexity (Sec. 9.3) of two Table 13 rows timed
@@ -812,6 +832,14 @@ def run_analysis(xr, ctx, args):
                       "bits_per_s": len(jobs) * c["N"] / (ms / 1e3),
                       "lowest_bits": {v: got[[k for k, (vv, b, _) in enumerate(jobs) if vv == v][0]]
                                       for v in c["variants"]}}
+    ops = recorded_lc_alu_ops()
+    if ops and ac:
+        # the Berlekamp-Massey kernel's ALU work at the ALU ceiling measured in
+        # this run, against the whole call (bit generation and host side included)
+        bound_ms = ops / ac["alu_lane_ops_per_s"] * 1e3
+        res["lc_bulk"]["alu_roofline"] = {"bound": "alu", "alu_lane_ops_per_call": ops, "alu_bound_ms": bound_ms,
+                                          "frac_of_call": bound_ms / ms,
+                                          "source": "profiles/berlekamp_massey__bulk_448x65536.txt"}
     assert ctx.status() == 0
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = analysis_cpu_baseline()

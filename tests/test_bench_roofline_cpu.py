@@ -26,8 +26,8 @@ def test_job_roofline_takes_the_slower_bound():
 
 
 def test_committed_summaries_match_the_current_sources():
-    """The ALU-ops, traffic and fused-kernel summaries under profiles/ were
-    taken on the current kernel sources (their recorded hashes match), so the
+    """The ALU-ops, traffic, fused-kernel and Berlekamp-Massey summaries under
+    profiles/ were taken on the current kernel sources (their recorded hashes match), so the
     bench applies them."""
     ops = bench.recorded_alu_ops()
     assert len(ops) == 36 and all(v > 0 for v in ops.values())
@@ -35,6 +35,8 @@ def test_committed_summaries_match_the_current_sources():
     assert t is not None and 0.9 < t["bytes_per_launch"] / t["algorithmic_bytes_per_launch"] <= 1.0
     f = bench.recorded_fused_counts()
     assert f is not None and f["alu_lane_ops_per_stream"] > 1000 and f["shared_wavefronts_per_stream"] > 16
+    lc = bench.recorded_lc_alu_ops()
+    assert lc is not None and lc > 1e10
 
 
 def test_fused_roofline_is_the_slowest_ceiling(monkeypatch):
